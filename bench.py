@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Benchmark: TPC clusters/s tracked on one GB300, batched vs plain, plus the adjoint calibration
+gradient cost (arxiv 1712.09434 section 3; Table 1 measures the same batched-vs-plain effect).
+
+One step = the whole hot path over the batched workload (64 events, multiplicity log-uniform in
+[100, 20000] tracks, 10 % loopers, 20 % noise, seeds 2000+e): tpc_track_batch (grid, neighbour
+finding, chains, following, selection, merge, FP32 Kalman refit; one CUDA graph) followed by
+tpc_refit_grad (refit + hand-written adjoint, FP64 reductions) on all tracks of the batch.
+value = clusters of the batch / step time.  Inputs are device-resident when the timed region
+starts; L2 is flushed (256 MB write) between timed steps.
+
+Also reported: the plain per-event form (tpc_track_event + tpc_refit_grad per event) on the same
+events, the adjoint cost per central event with an injected calibration, per-stage times, the
+roofline of the dominant stage, the oracle CPU baseline, and an end-to-end number through the
+binding with host buffers (H2D of the inputs and D2H of the results inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1712_09434_gb300 import synth  # noqa: E402
+
+METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
+WORKLOAD = "batch-64-events-logU-100-20000-tracks-20pct-noise"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------------------------
+
+def make_batch(n_events, seed0):
+    cache = os.path.join(tempfile.gettempdir(), "tpc_batch_%d_%d.npz" % (n_events, seed0))
+    if os.path.exists(cache):
+        z = np.load(cache, allow_pickle=False)
+        return dict(z)
+    t = time.time()
+    evs = [synth.make_event(c) for c in synth.batch_configs(n_events=n_events, seed0=seed0)]
+    b = synth.concat_events(evs)
+    d = dict(pad=b.pad_fp, tim=b.time_fp, bin_off=b.bin_off, ev_off=b.ev_off,
+             ev_bin_off=np.stack([e.bin_off for e in evs]))
+    np.savez(cache, **d)
+    log("generated %d events, %d clusters in %.1f s" % (n_events, b.n_clusters, time.time() - t))
+    return d
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), "tpc_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception as e:   # no nvidia-smi: report nothing rather than guess
+            log("clock sampling unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# native (CUDA) arm
+# ---------------------------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_native(args, rank, world):
+    import torch
+    from paper_1712_09434_gb300 import capi
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    seed0 = 2000 + 1000 * rank          # weak scaling: every rank tracks its own 64 events
+    d = make_batch(args.events, seed0)
+    n_clusters = int(d["pad"].shape[0])
+    n_ev = args.events
+    cl = capi.Clusters.from_numpy(d["pad"], d["tim"], d["bin_off"], n_ev)
+    cap_t = n_clusters // 8 + 1024
+    ctx = capi.Context(max_clusters=n_clusters, max_events=n_ev)
+    tr = capi.Tracks(n_clusters, n_ev, cap_t, n_clusters)
+    theta = torch.tensor(synth.theta_nominal(), dtype=torch.float64, device=dev)
+    s_chi2 = torch.empty(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(73, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    # calibration track selection (consistent tracks, nominal chi2/ndf < 5), fixed once: the
+    # tracks of a step are identical every step (the tracking is deterministic)
+    ctx.tpc_track_batch(cl, tr)
+    torch.cuda.synchronize()
+
+    def select(t, n):
+        ok = (t.ndf[:n] > 0) & (t.chi2[:n] < 5.0 * t.ndf[:n].float())
+        return ok.float().contiguous()
+
+    w_batch = select(tr, int(tr.n_tracks.item()))
+
+    def step():
+        ctx.tpc_track_batch(cl, tr)
+        ctx.tpc_refit_grad(cl, tr, theta, s_chi2, grad, w_batch)
+
+    def timed(fn, k, w, profile=False):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        st = ctx.tpc_sync_status()
+        if st != 0:
+            raise RuntimeError("device status %d" % st)
+        if profile:
+            ctx.tpc_profile_enable(True)
+            ctx.tpc_profile_read(reset=True)
+        total = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(k):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            if profile:
+                ctx.tpc_profile_read()
+        prof = None
+        if profile:
+            prof = ctx.tpc_profile_read(reset=True)
+            ctx.tpc_profile_enable(False)
+        return total / k, prof
+
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_step, prof = timed(step, args.steps, args.warmup, profile=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_all = ms_step
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_all = float(t.item())
+    st = ctx.tpc_sync_status()
+    assert st == 0, st
+    res = tr.to_host()
+    n_tracks, n_hits = res["n_tracks"], int(res["trk_off"][-1])
+
+    out = {"ms_step": ms_all, "n_clusters": n_clusters, "n_tracks": n_tracks, "n_hits": n_hits, "clocks": clk}
+    if rank != 0:
+        return out
+
+    # units for the algorithmic byte counts (outside the timed region)
+    nc_t = torch.empty(1, dtype=torch.int32, device=dev)
+    ctx.tpc_debug_copy(2, nc_t)
+    n_chains = int(nc_t.item())
+    cn = torch.empty(max(n_chains, 1), dtype=torch.int32, device=dev)
+    ctx.tpc_debug_copy(5, cn)
+    cand_hits = int(cn[:n_chains].sum().item())
+
+    # plain per-event form on the same events
+    evs_cl = []
+    for e in range(n_ev):
+        a, b = int(d["ev_off"][e]), int(d["ev_off"][e + 1])
+        evs_cl.append(capi.Clusters.from_numpy(d["pad"][a:b], d["tim"][a:b], d["ev_bin_off"][e], 1))
+    tr1 = capi.Tracks(n_clusters, 1, cap_t, n_clusters)
+    w_ev = []
+    for c in evs_cl:
+        ctx.tpc_track_event(c, tr1)
+        torch.cuda.synchronize()
+        w_ev.append(select(tr1, int(tr1.n_tracks.item())))
+
+    def plain():
+        for c, w in zip(evs_cl, w_ev):
+            ctx.tpc_track_event(c, tr1)
+            ctx.tpc_refit_grad(c, tr1, theta, s_chi2, grad, w)
+
+    ms_plain, _ = timed(plain, max(1, min(args.steps, 5)), 1)
+
+    # adjoint cost on a central event with an injected calibration
+    ev5 = synth.make_event(synth.calib_event())
+    c5 = capi.Clusters.from_numpy(ev5.pad_fp, ev5.time_fp, ev5.bin_off, 1)
+    t5 = capi.Tracks(ev5.n_clusters, 1, ev5.n_clusters // 8 + 1024, ev5.n_clusters)
+    ctx.tpc_track_event(c5, t5)
+    torch.cuda.synchronize()
+    w5 = select(t5, int(t5.n_tracks.item()))
+    th5 = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
+    ms_grad, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5), 10, 3)
+
+    # end to end through the binding with host (pinned) buffers
+    h_pad = torch.from_numpy(d["pad"]).pin_memory()
+    h_tim = torch.from_numpy(d["tim"].view(np.int16)).pin_memory()
+    h_bo = torch.from_numpy(d["bin_off"]).pin_memory()
+    h_label = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
+    h_off = torch.empty(cap_t + 1, dtype=torch.int32).pin_memory()
+    h_hits = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
+    h_par = torch.empty(cap_t * 5, dtype=torch.float32).pin_memory()
+    h_red = torch.empty(74, dtype=torch.float64).pin_memory()
+    d_pad, d_tim, d_bo = cl.pad_fp, cl.time_fp, cl.bin_off
+
+    def e2e():
+        d_pad.copy_(h_pad, non_blocking=True)
+        d_tim.copy_(h_tim, non_blocking=True)
+        d_bo.copy_(h_bo, non_blocking=True)
+        step()
+        h_label.copy_(tr.label[:n_clusters], non_blocking=True)
+        h_off.copy_(tr.trk_off[:cap_t + 1], non_blocking=True)
+        h_hits.copy_(tr.trk_hits[:n_clusters], non_blocking=True)
+        h_par.copy_(tr.par[:cap_t * 5], non_blocking=True)
+        h_red[:1].copy_(s_chi2, non_blocking=True)
+        h_red[1:].copy_(grad, non_blocking=True)
+
+    ms_e2e, _ = timed(e2e, max(1, min(args.steps, 5)), 1)
+    h2d = h_pad.numel() * 2 + h_tim.numel() * 2 + h_bo.numel() * 4
+    d2h = (h_label.numel() + h_off.numel() + h_hits.numel()) * 4 + h_par.numel() * 4 + h_red.numel() * 8
+
+    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), ms_e2e=ms_e2e,
+               h2d=h2d, d2h=d2h, prof=prof, n_chains=n_chains, cand_hits=cand_hits)
+    ctx.close()
+    return out
+
+
+# algorithmic bytes per stage (compulsory DRAM traffic of each stage's inputs and outputs)
+def stage_bytes(u):
+    N, C, Hc, T, Ht = u["n_clusters"], u["n_chains"], u["cand_hits"], u["n_tracks"], u["n_hits"]
+    return {
+        "grid": 10 * N,                 # read (pad, time) 4 B; write packed (Y, Z) 4 B + local index 2 B
+        "links": 18 * N,                # read own 4 B + neighbour-row grid 6 B; write up, down 8 B
+        "chains": 16 * N + 12 * C,      # read up/down 8 B, write/read chain length 8 B; chain records
+        "follow": 8 * Hc + 12 * C,      # candidate hit: slot write 4 B + cluster read 4 B; chain record
+        "select": 16 * Hc,              # candidate hit: slot read 4 B, claim 8 B, owner 4 B
+        "merge": 12 * Ht + 32 * C,      # track hit: slot read + hit and label write; segment ends
+        "refit": 8 * Ht + 92 * T,       # track hit: packed hit 8 B; per track 23 words out
+        "pack": 16 * Ht,                # hit index 4 B + cluster 4 B in, packed hit 8 B out
+        "refit_grad": 8 * Ht + 104 * T,  # packed hit 8 B; per-track record out
+        "reduce": 104 * T,
+    }
+
+
+def finish_native(args, res, world):
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    n_cl_total = res["n_clusters"] * world
+    value = n_cl_total / (res["ms_step"] * 1e-3)
+    prof, n_calls = res["prof"]
+    k = max(n_calls, 1)
+    stage_ms = {s: v / k for s, v in prof.items()}
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    byts = stage_bytes(res)
+    achieved = byts[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    plain_value = res["n_clusters"] / (res["ms_plain"] * 1e-3)
+    e2e_value = n_cl_total / (res["ms_e2e"] * 1e-3)
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_path):
+        tj = json.load(open(prof_path))
+        if tj.get("stage") == dom and tj.get("workload") == WORKLOAD:
+            traffic = tj.get("bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32+f32 (f64 reductions)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_events": args.events, "clusters_per_gpu": res["n_clusters"],
+                   "tracks_per_gpu": res["n_tracks"], "l2": "flushed (256 MB write) between timed steps",
+                   "step": "tpc_track_batch (CUDA graph) + tpc_refit_grad over the batch"},
+        "plain": {"value": plain_value, "unit": "clusters/s", "ms_per_step": res["ms_plain"],
+                  "form": "tpc_track_event + tpc_refit_grad per event, same 64 events"},
+        "batched_gain": value / world / plain_value,
+        "adjoint": {"value": res["ms_grad_event"] * 1e3, "unit": "us/event",
+                    "event": "central, 20000 tracks, injected calibration", "tracks": res["n_tracks_c5"]},
+        "stage_ms": stage_ms,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes": byts[dom]},
+        "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": res["h2d"],
+                "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": None,
+        "clocks": res["clocks"],
+    }
+    return line
+
+
+# ---------------------------------------------------------------------------------------------
+# oracle (CPU) arm
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(d, max_seconds):
+    """Time the FP64 oracle (tracking S2-S7 + refit S8) event by event until max_seconds of work;
+    returns (clusters, seconds, events)."""
+    from oracle import oracle as O
+    n = len(d["ev_off"]) - 1
+    done_cl, t_tot, k = 0, 0.0, 0
+    for e in range(n):
+        a, b = int(d["ev_off"][e]), int(d["ev_off"][e + 1])
+        pad, tim, bo = d["pad"][a:b], d["tim"][a:b], d["ev_bin_off"][e]
+        t = time.perf_counter()
+        r = O.track_event(pad, tim, bo)
+        O.fit(pad, tim, bo, r["trk_off"], r["trk_hits"])
+        t_tot += time.perf_counter() - t
+        done_cl += b - a
+        k += 1
+        if t_tot >= max_seconds:
+            break
+    return done_cl, t_tot, k
+
+
+def cpu_baseline(d, seconds=15.0):
+    from oracle import oracle as O
+    O.build()
+    cl, t, k = oracle_sample(d, seconds)
+    return {"value": cl / t, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d of the 64 events (%d clusters), tracking + FP64 refit, single thread" % (k, cl)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    d = make_batch(args.events, 2000)
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(d, 1.0)
+    tot_cl, tot_t = 0, 0.0
+    sample = None
+    for _ in range(args.steps):
+        cl, t, k = oracle_sample(d, 10.0)
+        tot_cl += cl
+        tot_t += t
+        sample = "first %d of the 64 events (%d clusters) per step" % (k, cl)
+    value = tot_cl / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_events": args.events},
+            "cpu_baseline": {"value": value, "unit": "clusters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--events", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    res = run_native(args, rank, world)
+    if rank == 0:
+        line = finish_native(args, res, world)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(make_batch(args.events, 2000))
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * tpc.h - C ABI of the GB300 (sm_103a) TPC track-reconstruction library.
+ *
+ * The library reconstructs charged-particle tracks in the 36 sectors of a time projection
+ * chamber, following the tracker of arxiv 1712.09434 section 3: cellular-automaton seeding on
+ * neighbouring pad rows (one thread per cluster), Kalman-filter track following and fitting (one
+ * thread per track), independent sectors whose track segments are merged afterwards, and a final
+ * Kalman refit.  It adds a hand-written adjoint of the refit that gives the gradient of the sum of
+ * chi2 with respect to calibration parameters (the online calibration feedback of sections 2 and
+ * 6), and batched tracking of many events in persistent kernels under a CUDA graph (the
+ * multi-event concurrency of section 3, Table 1).
+ *
+ * Conventions
+ *  - Every pointer in the structs below is a DEVICE pointer owned by the caller, unless stated.
+ *  - Calls are stream-ordered and asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *    is the legacy default stream).  The return code covers argument validation and launch
+ *    errors only.  Errors found on the device (capacity, timeout, bounds) are written to a status
+ *    word in the context; tpc_sync_status() waits for the stream and returns it.
+ *  - Return codes: TPC_OK (0) or a negative TPC_ERR_* value.  No call aborts or traps.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *
+ * Coordinates (fixed point; the reading of section 3 used by the integer decisions)
+ *  - pad_fp: local y of the cluster in its sector frame in units of lsb_cm (int16).
+ *  - time_fp: drift length (z_max - |z|) in units of lsb_cm (uint16, <= round(z_max/lsb_cm)).
+ *  - Clusters are sorted by (event, sector, row, pad_fp, time_fp); bin_off gives the cluster range
+ *    of every (event, sector, row) bin, bin = (event*n_sectors + sector)*n_rows + row.
+ */
+#ifndef TPC_H
+#define TPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPC_OK               0
+#define TPC_ERR_INVALID_ARG  -1   /* a pointer, size or struct field is invalid              */
+#define TPC_ERR_CAPACITY     -2   /* an output or workspace capacity is too small            */
+#define TPC_ERR_TIMEOUT      -3   /* a bounded device-side wait or iteration limit ran out   */
+#define TPC_ERR_CUDA         -4   /* a CUDA runtime call failed                              */
+#define TPC_ERR_BOUNDS       -5   /* an input index or coordinate is out of range            */
+#define TPC_ERR_NOT_RESERVED -6   /* the workspace is smaller than the call needs            */
+
+#define TPC_N_TUNE 8              /* kernels with tunable launch shape                       */
+#define TPC_N_PIPE_STAGES 7       /* grid, links, chains, follow, select, merge, refit        */
+#define TPC_N_REFIT_STAGES 3      /* pack, refit (+adjoint), reduce                           */
+
+/* Detector geometry (section 3; 159 pad rows at 85..247 cm, 18 sectors per side). */
+typedef struct {
+    int32_t n_sectors;        /* even; sectors [0, n/2) on the +z side, [n/2, n) on -z     */
+    int32_t n_rows;           /* pad rows per sector, 3..512                              */
+    double  x_first, x_last;  /* radii of the first and last row plane [cm], uniform pitch  */
+    double  half_angle_deg;   /* half opening angle of a sector [deg]                      */
+    double  z_max;            /* drift length [cm]                                         */
+    double  lsb_cm;           /* fixed-point unit of pad_fp and time_fp [cm]               */
+} tpc_geometry;
+
+/* Clusters of one event (n_events = 1) or of a batch of events (concatenated, see above). */
+typedef struct {
+    const int16_t  *pad_fp;   /* [n_clusters]                                              */
+    const uint16_t *time_fp;  /* [n_clusters]                                              */
+    const int32_t  *bin_off;  /* [n_events*n_sectors*n_rows + 1], nondecreasing, from 0    */
+    int32_t n_events;
+    int32_t n_clusters;
+} tpc_clusters;
+
+/* Track output, written by tpc_track_event / tpc_track_batch (caller-owned device buffers).
+ * Tracks are ordered by event, then by the index of their first segment's seed chain; hits are
+ * cluster indices in track order (segments along the merge chain, ascending rows inside a
+ * segment).  par = (y, z, sin phi, tan lambda, q/pT) at local x = xref in the frame of the first
+ * hit's sector; cov = 15-element lower triangle, row-major; chi2 in FP32; ndf = 2*n_hits - 5, or 0
+ * if the fit failed (then par, cov, chi2 are 0). */
+typedef struct {
+    int32_t *label;           /* [n_clusters]     track index or -1                        */
+    int32_t *trk_off;         /* [cap_tracks + 1] hit range of each track                  */
+    int32_t *trk_hits;        /* [cap_hits]       cluster indices                          */
+    int32_t *ev_trk_off;      /* [n_events + 1]   track range of each event                */
+    float   *par;             /* [cap_tracks*5]                                           */
+    float   *xref;            /* [cap_tracks]                                             */
+    float   *cov;             /* [cap_tracks*15]                                          */
+    float   *chi2;            /* [cap_tracks]                                             */
+    int32_t *ndf;             /* [cap_tracks]                                             */
+    int32_t *n_tracks;        /* [1]  total number of tracks (device scalar)               */
+    int32_t  cap_tracks;
+    int32_t  cap_hits;
+} tpc_tracks;
+
+/* Launch shape of the tunable kernels (0 = library default).  Index: 0 grid, 1 links, 2 chains,
+ * 3 follow, 4 select, 5 merge, 6 refit, 7 refit_grad.  block = threads per CTA (multiple of 32),
+ * ctas_per_sm = persistent CTAs per SM, chunk = work items taken per queue grab. */
+typedef struct {
+    int32_t block[TPC_N_TUNE];
+    int32_t ctas_per_sm[TPC_N_TUNE];
+    int32_t chunk[TPC_N_TUNE];
+} tpc_tuning;
+
+typedef struct tpc_ctx tpc_ctx;
+
+/* Create a context on the current CUDA device.  Bz in tesla.  Geometry tables are derived on the
+ * host and uploaded.  *out receives the context.  Errors: INVALID_ARG, CUDA. */
+int tpc_init(const tpc_geometry *geom, double bz_tesla, tpc_ctx **out);
+
+/* Size the library-owned workspace for calls of up to max_clusters clusters and max_events
+ * events (grows, never shrinks; allocation happens only here and in tpc_init).  Any call whose
+ * size exceeds the reservation fails with TPC_ERR_NOT_RESERVED.  Errors: INVALID_ARG, CUDA. */
+int tpc_reserve(tpc_ctx *ctx, int32_t max_clusters, int32_t max_events);
+
+/* Release the context and its workspace.  NULL is ignored. */
+void tpc_destroy(tpc_ctx *ctx);
+
+/* Track one or more events with one launch per step (the plain, per-event form; no graph).
+ * Steps: grid, neighbour finding, link cleaning and chains, following, selection, merge, refit at
+ * the nominal calibration.  `in` and `out` as documented above.  Errors: INVALID_ARG,
+ * NOT_RESERVED, CUDA; device-side errors via tpc_sync_status. */
+int tpc_track_event(tpc_ctx *ctx, const tpc_clusters *in, tpc_tracks *out, void *stream);
+
+/* Same result as tpc_track_event (bit-identical hit assignment), for a batch of events: the same
+ * persistent work-queue kernels, captured once into a CUDA graph and replayed.  The graph is keyed
+ * by the complete argument set (buffers, sizes, tuning); a call with different arguments captures
+ * again and updates the executable graph in place.  tune may be NULL (library defaults). */
+int tpc_track_batch(tpc_ctx *ctx, const tpc_clusters *in, tpc_tracks *out, const tpc_tuning *tune,
+                    void *stream);
+
+/* Kalman refit of the tracks in `trk` (trk_off, trk_hits and n_tracks as written by a tracking
+ * call on the same clusters; the other output pointers are not used) with clusters transformed
+ * under calibration theta = [s_vd, d_0..d_{ns-1}, a_0..a_{ns-1}] (1 + 2*n_sectors doubles, device).
+ * Transform: z = side*(z_max - s_vd*D) + d_k and (x, y) = (x_r, y)*(1 + a_k*(rho - x_first)/
+ * ((x_last - x_first)*rho)), rho = |(x_r, y)|.  Objective: sum over fitted tracks of
+ * weight[t]*chi2[t] (weight: device float [n_tracks], or NULL for all 1; a track of weight 0 is
+ * skipped), written to *sum_chi2 (device double); if grad is not NULL, its gradient
+ * d(objective)/d(theta) (device, 1 + 2*n_sectors doubles) from the adjoint of the refit.  FP32
+ * Kalman arithmetic; FP64 cross-track reductions in a fixed order (deterministic).
+ * Errors: INVALID_ARG, NOT_RESERVED, CUDA; device-side errors via tpc_sync_status. */
+int tpc_refit_grad(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, const double *theta,
+                   const float *weight, double *sum_chi2, double *grad, void *stream);
+
+/* Wait for `stream` and return the device status word of the last calls (then clear it). */
+int tpc_sync_status(tpc_ctx *ctx, void *stream);
+
+/* Static description of a return code. */
+const char *tpc_strerror(int code);
+
+/* Copy an internal intermediate of the last tracking call to `dst` (device, caller-owned) for
+ * step-by-step parity tests (int32 arrays; N = reserved clusters, C = chain capacity):
+ * 0 up[N], 1 down[N] (neighbour links, -1 = none), 2 n_chains[1], 3 chain_start[C],
+ * 4 chain_len[C], 5 cand_n[C], 6 cand_slots[C*n_rows] (cluster per row, -1 = miss, valid inside
+ * the candidate's row range), 7 cand_rows[C] (first row | last row << 16), 8 seg_n[C] (kept hits,
+ * 0 if rejected), 9 next[C] (merge successor or -1), 10 counters[16] (0 chains, 1 tracks, 2 hits,
+ * 3 largest number of selection rounds).  At most dst_bytes bytes are copied. */
+int tpc_debug_copy(tpc_ctx *ctx, int32_t what, void *dst, int64_t dst_bytes, void *stream);
+
+/* Per-stage timing.  tpc_profile_enable(ctx, 1) makes later calls record CUDA events between their
+ * stages on the call's stream (inside the CUDA graph for tpc_track_batch).  tpc_profile_read waits
+ * for the last profiled calls, adds their stage times to per-context sums and copies the sums
+ * (milliseconds) to ms[0..cap): the TPC_N_PIPE_STAGES tracking stages, then the
+ * TPC_N_REFIT_STAGES refit stages; *n_calls (may be NULL) receives the number of tracking calls
+ * summed.  Only the last call of each kind since the previous read is counted, so read after every
+ * call.  A negative cap resets the sums (nothing is copied).  Returns the number of stages. */
+int tpc_profile_enable(tpc_ctx *ctx, int enable);
+int tpc_profile_read(tpc_ctx *ctx, double *ms, int32_t cap, int32_t *n_calls);
+
+/* Reading constants of the integer track finding, for comparison with an independent
+ * implementation: W_LINK, D_MAX, N_SEED, M_MISS, W_F0, W_F1, V_MAX, N_MIN, W_MERGE, MERGE_XMAX,
+ * MERGE_BACK.  Returns the count written (at most cap). */
+int tpc_constants(int64_t *out, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPC_H */

@@ -181,27 +181,40 @@ def fit(pad, tim, bin_off, trk_off, trk_hits, theta=None, g=None):
     return dict(par=par[:nt], xref=xref[:nt], cov=cov[:nt], chi2=chi2[:nt], ndf=ndf[:nt])
 
 
-def chi2_total(pad, tim, bin_off, trk_off, trk_hits, theta, g=None):
+def _weights(weight, n_trk):
+    if weight is None:
+        return None
+    w = np.ascontiguousarray(weight, np.float64)
+    assert w.shape[0] >= n_trk
+    return w
+
+
+def chi2_total(pad, tim, bin_off, trk_off, trk_hits, theta, g=None, weight=None):
+    """Weighted sum of chi2 (weight per track, None = 1) of the FP64 refit at calibration theta."""
     gg = g if g is not None else geometry()
     th = np.ascontiguousarray(theta, np.float64)
+    nt = trk_off.shape[0] - 1
+    w = _weights(weight, nt)
     return lib().or_chi2_total(ctypes.byref(gg), _p(np.ascontiguousarray(pad, np.int16)),
                                _p(np.ascontiguousarray(tim, np.uint16)), _p(np.ascontiguousarray(bin_off, np.int32)),
-                               ctypes.c_int32(pad.shape[0]), ctypes.c_int32(trk_off.shape[0] - 1),
+                               ctypes.c_int32(pad.shape[0]), ctypes.c_int32(nt),
                                _p(np.ascontiguousarray(trk_off, np.int32)), _p(np.ascontiguousarray(trk_hits, np.int32)),
-                               _p(th))
+                               _p(w) if w is not None else ctypes.c_void_p(0), _p(th))
 
 
-def grad_fd(pad, tim, bin_off, trk_off, trk_hits, theta, h=(1e-6, 1e-4, 1e-4), g=None):
-    """Reference gradient d(sum chi2)/d(theta) by FP64 central differences."""
+def grad_fd(pad, tim, bin_off, trk_off, trk_hits, theta, h=(1e-6, 1e-4, 1e-4), g=None, weight=None):
+    """Reference gradient d(sum w chi2)/d(theta) by FP64 central differences."""
     gg = g if g is not None else geometry()
     th = np.ascontiguousarray(theta, np.float64)
+    nt = trk_off.shape[0] - 1
+    w = _weights(weight, nt)
     grad = np.empty(1 + 2 * gg.n_sectors)
     hh = np.asarray(h, np.float64)
     rc = lib().or_grad_fd(ctypes.byref(gg), _p(np.ascontiguousarray(pad, np.int16)),
                           _p(np.ascontiguousarray(tim, np.uint16)), _p(np.ascontiguousarray(bin_off, np.int32)),
-                          ctypes.c_int32(pad.shape[0]), ctypes.c_int32(trk_off.shape[0] - 1),
+                          ctypes.c_int32(pad.shape[0]), ctypes.c_int32(nt),
                           _p(np.ascontiguousarray(trk_off, np.int32)), _p(np.ascontiguousarray(trk_hits, np.int32)),
-                          _p(th), _p(hh), _p(grad))
+                          _p(w) if w is not None else ctypes.c_void_p(0), _p(th), _p(hh), _p(grad))
     assert rc == 0, rc
     return grad
 

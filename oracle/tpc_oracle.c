@@ -323,12 +323,13 @@ int or_select(int32_t n, int32_t n_rows, int32_t n_cand, const int32_t *cand_hit
  * (D, index)) are linked S -> T.  next[] receives the links. */
 static int merge_match(const or_geom *g, const int16_t *pad, const uint16_t *tim, const int32_t *bins,
                        const int32_t *hs, int ns, const int32_t *ht, int64_t *D_out) {
+    int half = g->n_sectors / 2;
     int ks = bins[hs[ns - 1]] / g->n_rows, kt = bins[ht[0]] / g->n_rows;
-    int k18s = ks % 18, k18t = kt % 18;
+    int hs_ = ks % half, ht_ = kt % half;
     int sgn;
-    if ((ks < 18) != (kt < 18)) return 0;
-    if ((k18s + 1) % 18 == k18t) sgn = +1;
-    else if ((k18t + 1) % 18 == k18s) sgn = -1;
+    if ((ks < half) != (kt < half)) return 0;
+    if ((hs_ + 1) % half == ht_) sgn = +1;           /* T is the next sector in phi      */
+    else if ((ht_ + 1) % half == hs_) sgn = -1;      /* T is the previous sector in phi  */
     else return 0;
     int32_t hL = hs[ns - 1], hB = hs[ns - 1 - OR_MERGE_BACK];
     int64_t X2 = g->xtab[bins[hL] % g->n_rows], Y2 = pad[hL], Z2 = tim[hL];
@@ -451,7 +452,7 @@ done:
  * ========================================================================================== */
 typedef struct { double x, y, z; } or_pt;
 
-static double sector_alpha(const or_geom *g, int k) { return ((k % 18) + 0.5) * 2.0 * g->half_angle; }
+static double sector_alpha(const or_geom *g, int k) { return ((k % (g->n_sectors / 2)) + 0.5) * 2.0 * g->half_angle; }
 
 static or_pt transform(const or_geom *g, double x_first, double span, int k, int r, int64_t Y, int64_t Z,
                        const double *th) {
@@ -610,15 +611,22 @@ static int kf_seed(const or_geom *g, const or_pt *pa, int ka, const or_pt *pb, i
     return 1;
 }
 
-static const double OR_C0[5] = {100.0, 100.0, 1.0, 1.0, 100.0};
+/* Prior covariance of the seed state: sigma = 1 cm (y, z), 0.1 (sin phi, tan lambda), 1 c/GeV (q/pT).
+ * Weak against the data of a track (posterior sigmas ~0.05 cm, ~1e-3, ~1e-2 c/GeV), and a
+ * dynamic range an FP32 filter can carry (the refit on the GPU is FP32). */
+static const double OR_C0[5] = {1.0, 1.0, 0.01, 0.01, 1.0};
 
-/* Fit given points: measurements m[i] in the frame of sector ks[i] (hit order of the track), seed
- * from the nominal points a, b, e (first, middle, last hit).  Returns 1 on success. */
+/* Fit given points: measurements m[i] in the frame of sector ks[i] (hit order of the track).  The
+ * seed takes sin phi, tan lambda and q/pT from the circle through the nominal points a, b, e
+ * (first, middle, last hit) and its position from the last measurement.  Returns 1 on success. */
 static int fit_points(const or_geom *g, int nh, const int *ks, const or_pt *m, const or_pt *a, const or_pt *b,
                       const or_pt *e, or_kf *s) {
     memset(s, 0, sizeof(*s));
     if (!kf_seed(g, a, ks[0], b, ks[(nh - 1) / 2], e, ks[nh - 1], s->p)) return 0;
-    s->x = e->x;
+    /* direction and curvature from the nominal circle; position at the last measurement itself */
+    s->x = m[nh - 1].x;
+    s->p[0] = m[nh - 1].y;
+    s->p[1] = m[nh - 1].z;
     s->frame = ks[nh - 1];
     s->ok = 1;
     for (int i = 0; i < 5; i++) s->P[i][i] = OR_C0[i];
@@ -680,38 +688,43 @@ int or_fit(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const
     return 0;
 }
 
-/* S9 reference: sum of chi2 over all tracks that fit, at calibration theta.  If `only_sector` >= 0,
- * only tracks with a hit in that sector are summed (used by the finite differences below). */
+/* S9 reference: weighted sum of chi2 over the tracks that fit, at calibration theta.  weight may be
+ * NULL (all 1); `use` (may be NULL) restricts the sum to flagged tracks (used by the differences
+ * below, which only refit the tracks a parameter can change). */
 static double chi2_sum(const or_geom *g, double x_first, double span, const int16_t *pad, const uint16_t *tim,
                        const int32_t *bins, int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits,
-                       const char *use, const double *theta) {
+                       const double *weight, const char *use, const double *theta) {
     double sum = 0.0;
     for (int32_t t = 0; t < n_trk; t++) {
         if (use && !use[t]) continue;
+        const double w = weight ? weight[t] : 1.0;
+        if (w == 0.0) continue;
         or_kf s;
         int nh = trk_off[t + 1] - trk_off[t];
-        if (nh >= 3 && fit_track(g, x_first, span, pad, tim, bins, trk_hits + trk_off[t], nh, theta, &s)) sum += s.chi2;
+        if (nh >= 3 && fit_track(g, x_first, span, pad, tim, bins, trk_hits + trk_off[t], nh, theta, &s))
+            sum += w * s.chi2;
     }
     return sum;
 }
 
 double or_chi2_total(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
-                     int32_t n, int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits, const double *theta) {
+                     int32_t n, int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits, const double *weight,
+                     const double *theta) {
     or_geom g;
     if (make_geom(gin, &g)) return -1.0;
     int32_t *bins = cluster_bins(bin_off, g.n_sectors * g.n_rows, n);
     double v = chi2_sum(&g, gin->x_first, gin->x_last - gin->x_first, pad, tim, bins, n_trk, trk_off, trk_hits,
-                        NULL, theta);
+                        weight, NULL, theta);
     free(bins);
     return v;
 }
 
-/* Gradient of the chi2 sum by central differences in double precision: the plain definition of
- * the derivative.  Steps h[0] (s_vd), h[1] (d_k), h[2] (a_k).  Only tracks touching the perturbed
- * sector are refitted for d_k and a_k (the others do not depend on them). */
+/* Gradient of the weighted chi2 sum by central differences in double precision: the plain
+ * definition of the derivative.  Steps h[0] (s_vd), h[1] (d_k), h[2] (a_k).  Only tracks touching
+ * the perturbed sector are refitted for d_k and a_k (the others do not depend on them). */
 int or_grad_fd(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off, int32_t n,
-               int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits, const double *theta,
-               const double *h, double *grad) {
+               int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits, const double *weight,
+               const double *theta, const double *h, double *grad) {
     or_geom g;
     if (make_geom(gin, &g)) return -1;
     int ns = g.n_sectors, np = 1 + 2 * ns;
@@ -730,9 +743,9 @@ int or_grad_fd(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, c
         }
         memcpy(th, theta, sizeof(double) * np);
         th[j] = theta[j] + hj;
-        double fp = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, use, th);
+        double fp = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, weight, use, th);
         th[j] = theta[j] - hj;
-        double fm = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, use, th);
+        double fm = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, weight, use, th);
         grad[j] = (fp - fm) / (2.0 * hj);
     }
     free(th); free(use); free(bins);

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of the C ABI in include/tpc.h (argument marshalling only).
+
+Every step of the tracking and of the refit runs in the CUDA kernels of ``libtpc.so``; torch is
+used here for device memory, streams and ``torch.autograd.Function``.  Importing this module
+raises if the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtpc.so")
+
+TPC_OK = 0
+TPC_ERR_INVALID_ARG = -1
+TPC_ERR_CAPACITY = -2
+TPC_ERR_TIMEOUT = -3
+TPC_ERR_CUDA = -4
+TPC_ERR_BOUNDS = -5
+TPC_ERR_NOT_RESERVED = -6
+TPC_N_TUNE = 8
+STAGES = ["grid", "links", "chains", "follow", "select", "merge", "refit", "pack", "refit_grad", "reduce"]
+
+
+class tpc_geometry(ctypes.Structure):
+    _fields_ = [("n_sectors", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("x_first", ctypes.c_double),
+                ("x_last", ctypes.c_double), ("half_angle_deg", ctypes.c_double), ("z_max", ctypes.c_double),
+                ("lsb_cm", ctypes.c_double)]
+
+
+class tpc_clusters(ctypes.Structure):
+    _fields_ = [("pad_fp", ctypes.c_void_p), ("time_fp", ctypes.c_void_p), ("bin_off", ctypes.c_void_p),
+                ("n_events", ctypes.c_int32), ("n_clusters", ctypes.c_int32)]
+
+
+class tpc_tracks(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_void_p), ("trk_off", ctypes.c_void_p), ("trk_hits", ctypes.c_void_p),
+                ("ev_trk_off", ctypes.c_void_p), ("par", ctypes.c_void_p), ("xref", ctypes.c_void_p),
+                ("cov", ctypes.c_void_p), ("chi2", ctypes.c_void_p), ("ndf", ctypes.c_void_p),
+                ("n_tracks", ctypes.c_void_p), ("cap_tracks", ctypes.c_int32), ("cap_hits", ctypes.c_int32)]
+
+
+class tpc_tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32 * TPC_N_TUNE), ("ctas_per_sm", ctypes.c_int32 * TPC_N_TUNE),
+                ("chunk", ctypes.c_int32 * TPC_N_TUNE)]
+
+
+class TpcError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__("%s: %s (%d)" % (what, _lib.tpc_strerror(code).decode(), code))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libtpc.so is not built (run paper_1712_09434_gb300.build.build()); "
+                          "there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.tpc_init.argtypes = [ctypes.POINTER(tpc_geometry), ctypes.c_double, ctypes.POINTER(vp)]
+    lib.tpc_reserve.argtypes = [vp, i32, i32]
+    lib.tpc_destroy.argtypes = [vp]
+    lib.tpc_destroy.restype = None
+    lib.tpc_track_event.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp]
+    lib.tpc_track_batch.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks),
+                                    ctypes.POINTER(tpc_tuning), vp]
+    lib.tpc_refit_grad.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp, vp, vp]
+    lib.tpc_sync_status.argtypes = [vp, vp]
+    lib.tpc_strerror.argtypes = [ctypes.c_int]
+    lib.tpc_strerror.restype = ctypes.c_char_p
+    lib.tpc_debug_copy.argtypes = [vp, i32, vp, i64, vp]
+    lib.tpc_constants.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
+    lib.tpc_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.tpc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(i32)]
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def check(code, what=""):
+    if code != TPC_OK:
+        raise TpcError(code, what)
+
+
+def constants():
+    buf = (ctypes.c_int64 * 32)()
+    n = _lib.tpc_constants(buf, 32)
+    names = ["W_LINK", "D_MAX", "N_SEED", "M_MISS", "W_F0", "W_F1", "V_MAX", "N_MIN", "W_MERGE",
+             "MERGE_XMAX", "MERGE_BACK"]
+    return dict(zip(names, [buf[i] for i in range(n)]))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Clusters:
+    """Device-resident clusters of one event or a batch (see tpc_clusters)."""
+
+    def __init__(self, pad_fp, time_fp, bin_off, n_events):
+        self.pad_fp = pad_fp
+        self.time_fp = time_fp
+        self.bin_off = bin_off
+        self.n_events = int(n_events)
+        self.n_clusters = int(pad_fp.shape[0])
+
+    @staticmethod
+    def from_numpy(pad_fp, time_fp, bin_off, n_events=1, device="cuda"):
+        """time_fp (uint16) travels as an int16 tensor with the same bits."""
+        import numpy as np
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=device)
+        return Clusters(t(pad_fp.astype(np.int16)), t(time_fp.astype(np.uint16).view(np.int16)),
+                        t(bin_off.astype(np.int32)), n_events)
+
+    def struct(self):
+        return tpc_clusters(_ptr(self.pad_fp), _ptr(self.time_fp), _ptr(self.bin_off), self.n_events,
+                            self.n_clusters)
+
+
+class Tracks:
+    """Caller-owned device output buffers (see tpc_tracks)."""
+
+    def __init__(self, n_clusters, n_events, cap_tracks, cap_hits, device="cuda"):
+        z = lambda n, dt: torch.empty(max(int(n), 1), dtype=dt, device=device)
+        self.label = z(n_clusters, torch.int32)
+        self.trk_off = z(cap_tracks + 1, torch.int32)
+        self.trk_hits = z(cap_hits, torch.int32)
+        self.ev_trk_off = z(n_events + 1, torch.int32)
+        self.par = z(cap_tracks * 5, torch.float32)
+        self.xref = z(cap_tracks, torch.float32)
+        self.cov = z(cap_tracks * 15, torch.float32)
+        self.chi2 = z(cap_tracks, torch.float32)
+        self.ndf = z(cap_tracks, torch.int32)
+        self.n_tracks = z(1, torch.int32)
+        self.cap_tracks = int(cap_tracks)
+        self.cap_hits = int(cap_hits)
+
+    def struct(self):
+        return tpc_tracks(_ptr(self.label), _ptr(self.trk_off), _ptr(self.trk_hits), _ptr(self.ev_trk_off),
+                          _ptr(self.par), _ptr(self.xref), _ptr(self.cov), _ptr(self.chi2), _ptr(self.ndf),
+                          _ptr(self.n_tracks), self.cap_tracks, self.cap_hits)
+
+    def to_host(self):
+        """Copy the result to numpy (synchronises)."""
+        nt = int(self.n_tracks.item())
+        off = self.trk_off[:nt + 1].cpu().numpy()
+        return dict(n_tracks=nt, trk_off=off, trk_hits=self.trk_hits[:int(off[-1])].cpu().numpy(),
+                    label=self.label.cpu().numpy(), ev_trk_off=self.ev_trk_off.cpu().numpy(),
+                    par=self.par[:5 * nt].view(-1, 5).cpu().numpy(), xref=self.xref[:nt].cpu().numpy(),
+                    cov=self.cov[:15 * nt].view(-1, 15).cpu().numpy(), chi2=self.chi2[:nt].cpu().numpy(),
+                    ndf=self.ndf[:nt].cpu().numpy())
+
+
+def default_geometry():
+    return tpc_geometry(36, 159, 85.0, 247.0, 10.0, 250.0, 1.0 / 128.0)
+
+
+class Context:
+    """tpc_init / tpc_reserve / tpc_destroy."""
+
+    def __init__(self, geometry=None, bz_tesla=0.5, max_clusters=0, max_events=1):
+        self.geometry = geometry if geometry is not None else default_geometry()
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        check(_lib.tpc_init(ctypes.byref(self.geometry), ctypes.c_double(bz_tesla), ctypes.byref(h)), "tpc_init")
+        self.handle = h
+        if max_clusters > 0:
+            self.reserve(max_clusters, max_events)
+
+    def reserve(self, max_clusters, max_events=1):
+        check(_lib.tpc_reserve(self.handle, int(max_clusters), int(max_events)), "tpc_reserve")
+
+    def close(self):
+        if self.handle:
+            _lib.tpc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- entry points (same names as the C ABI) ---
+    def tpc_track_event(self, clusters, tracks, stream=None):
+        cs, ts = clusters.struct(), tracks.struct()
+        check(_lib.tpc_track_event(self.handle, ctypes.byref(cs), ctypes.byref(ts), _stream(stream)),
+              "tpc_track_event")
+
+    def tpc_track_batch(self, clusters, tracks, tuning=None, stream=None):
+        cs, ts = clusters.struct(), tracks.struct()
+        tp = ctypes.byref(tuning) if tuning is not None else ctypes.POINTER(tpc_tuning)()
+        check(_lib.tpc_track_batch(self.handle, ctypes.byref(cs), ctypes.byref(ts), tp, _stream(stream)),
+              "tpc_track_batch")
+
+    def tpc_refit_grad(self, clusters, tracks, theta, sum_chi2, grad=None, weight=None, stream=None):
+        cs, ts = clusters.struct(), tracks.struct()
+        check(_lib.tpc_refit_grad(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(theta), _ptr(weight),
+                                  _ptr(sum_chi2), _ptr(grad), _stream(stream)), "tpc_refit_grad")
+
+    def tpc_sync_status(self, stream=None):
+        return _lib.tpc_sync_status(self.handle, _stream(stream))
+
+    def tpc_profile_enable(self, enable=True):
+        check(_lib.tpc_profile_enable(self.handle, 1 if enable else 0), "tpc_profile_enable")
+
+    def tpc_profile_read(self, reset=False):
+        """(stage name -> summed ms, number of tracking calls) since the last reset."""
+        buf = (ctypes.c_double * 16)()
+        nc = ctypes.c_int32(0)
+        n = _lib.tpc_profile_read(self.handle, buf, 16, ctypes.byref(nc))
+        if n < 0:
+            check(n, "tpc_profile_read")
+        out = dict(zip(STAGES, [buf[i] for i in range(n)])), nc.value
+        if reset:
+            _lib.tpc_profile_read(self.handle, buf, -1, None)
+        return out
+
+    def tpc_debug_copy(self, what, dst, stream=None):
+        check(_lib.tpc_debug_copy(self.handle, int(what), _ptr(dst), dst.numel() * dst.element_size(),
+                                  _stream(stream)), "tpc_debug_copy")
+
+
+class CalibRefit(torch.autograd.Function):
+    """sum_t w_t chi2_t of the Kalman refit as a differentiable function of the calibration theta
+    (float64, [1 + 2*n_sectors]); weight (float32 [n_tracks] or None) selects the tracks.  The
+    forward call computes the adjoint gradient as well; backward scales it."""
+
+    @staticmethod
+    def forward(ctx_, theta, context, clusters, tracks, weight=None):
+        theta = theta.detach().to(dtype=torch.float64).contiguous()
+        out = torch.empty(1, dtype=torch.float64, device=theta.device)
+        grad = torch.empty_like(theta)
+        context.tpc_refit_grad(clusters, tracks, theta, out, grad, weight)
+        ctx_.save_for_backward(grad)
+        return out[0]
+
+    @staticmethod
+    def backward(ctx_, g):
+        (grad,) = ctx_.saved_tensors
+        return g * grad, None, None, None, None

@@ -1,0 +1,173 @@
+// S5 track following: Kalman-filter following of each seed across the pad rows, one thread per
+// track candidate (arxiv 1712.09434 section 3).  Every accept/reject decision is taken by an
+// integer steady-state Kalman filter (alpha-beta-gamma = 1/2, 1/8, 1/32 on a Q16 state, floor
+// shifts, int64) so that the hit lists are bit-identical to an independent FP64 implementation;
+// the floating-point Kalman filter is used for the parameters only (S8).
+//
+// The filter runs along the whole chain, then extends it row by row outwards, then (re-initialised
+// from the other end) inwards: predict, look up the nearest cluster (minimum (d^2, index)) within a
+// radius that grows with consecutive misses in the row's Z-slab grid, update.  A candidate is
+// stored as one cluster per row (-1 for a miss) between its first and last row.
+#include "tpc_common.cuh"
+
+namespace tpc {
+
+namespace {
+
+struct Abg {
+    long long p, v, a;
+};
+
+__device__ __forceinline__ void abg_init(Abg &f, long long m0, long long m1) {
+    f.p = m0 * 65536;
+    f.v = (m1 - m0) * 65536;
+    f.a = 0;
+}
+__device__ __forceinline__ void abg_predict(Abg &f) {
+    f.p += f.v + (f.a >> 1);
+    f.v += f.a;
+}
+__device__ __forceinline__ void abg_update(Abg &f, long long m) {
+    const long long e = m * 65536 - f.p;
+    f.p += e >> 1;
+    f.v += e >> 3;
+    f.a += e >> 5;
+}
+__device__ __forceinline__ int q16_round(long long p) { return (int)((p + 32768) >> 16); }
+__device__ __forceinline__ int slab_of(int z) { int s = z >> ZB_SHIFT; return s < NZB - 1 ? s : NZB - 1; }
+
+__device__ __forceinline__ int lower_y(const int32_t *yz, int lo, int hi, int y) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)(int16_t)(__ldg(yz + mid) & 0xffff) < y) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Nearest cluster of a row bin to (py, pz) with d^2 <= w^2: row-local index, or -1.
+__device__ int nearest(const Work &W, int bin, int py, int pz, int w) {
+    const int c0 = __ldg(W.bin_off + bin);
+    const int32_t *yz = W.gyz + pstart_of(c0, bin);
+    const uint16_t *loc = W.gloc + pstart_of(c0, bin);
+    const uint16_t *zo = W.zoff + (size_t)bin * ZOFF_STRIDE;
+    const int zl = slab_of(max(pz - w, 0)), zh = slab_of(pz + w);
+    const long long w2 = (long long)w * w;
+    long long bd = w2 + 1;
+    int bl = 0x7fffffff;
+    for (int s = zl; s <= zh; s++) {
+        const int hi = __ldg(zo + s + 1);
+        for (int i = lower_y(yz, __ldg(zo + s), hi, py - w); i < hi; i++) {
+            const int32_t v = __ldg(yz + i);
+            const int y = (int16_t)(v & 0xffff);
+            if (y > py + w) break;
+            const long long dy = y - py, dz = (int)((uint32_t)v >> 16) - pz;
+            const long long d2 = dy * dy + dz * dz;
+            if (d2 > w2) continue;
+            const int l = __ldg(loc + i);
+            if (d2 < bd || (d2 == bd && l < bl)) { bd = d2; bl = l; }
+        }
+    }
+    return bl == 0x7fffffff ? -1 : bl;
+}
+
+// Extend from the filter state (already at row `row_last`) in direction dir; writes slots.
+// Returns the number of clusters found and the row of the last one in *row_end.
+__device__ int extend(const Work &W, const DevGeom &g, Abg &fy, Abg &fz, int rowbase_bin, int row_last, int dir,
+                      int32_t *slots, int *row_end) {
+    int n = 0, misses = 0;
+    *row_end = row_last;
+    for (int row = row_last + dir; row >= 0 && row < g.n_rows; row += dir) {
+        abg_predict(fy);
+        abg_predict(fz);
+        const int py = q16_round(fy.p), pz = q16_round(fz.p);
+        const long long av = fy.v < 0 ? -fy.v : fy.v;
+        if (abs(py) > g.ymax[row] || pz < 0 || pz > g.zmax || av > (long long)V_MAX * 65536) break;
+        const int w = W_F0 + W_F1 * misses;
+        const int l = nearest(W, rowbase_bin + row, py, pz, w);
+        if (l >= 0) {
+            const int h = __ldg(W.bin_off + rowbase_bin + row) + l;
+            abg_update(fy, __ldg(W.pad + h));
+            abg_update(fz, __ldg(W.tim + h));
+            slots[row] = h;
+            *row_end = row;
+            n++;
+            misses = 0;
+        } else {
+            slots[row] = -1;
+            if (++misses >= M_MISS) break;
+        }
+    }
+    return n;
+}
+
+__global__ void __launch_bounds__(128) k_follow(Work W) {
+    __shared__ int s_item;
+    const DevGeom &g = *W.geom;
+    const int nr = g.n_rows;
+    int n_chains = W.counters[CNT_NCHAINS];
+    if (n_chains > W.cap_chains) n_chains = W.cap_chains;
+    const int chunk = blockDim.x * (W.tune.chunk[3] > 0 ? W.tune.chunk[3] : 1);
+    int32_t *q = W.counters + CNT_Q0 + 3;
+    for (int base = queue_next(q, chunk, &s_item); base < n_chains; base = queue_next(q, chunk, &s_item)) {
+        for (int t = base + threadIdx.x; t < base + chunk && t < n_chains; t += blockDim.x) {
+            const int start = W.chain_start[t], len = W.chain_len[t], bin = W.chain_bin[t];
+            const int row0 = bin % nr;
+            const int rowbase = bin - row0;
+            int32_t *slots = W.cand_slots + (size_t)t * nr;
+            // filter along the chain in ascending rows, writing the chain hits
+            Abg fy, fz;
+            int x = start, m0y = 0, m0z = 0;
+            for (int k = 0; k < len; k++) {
+                const int y = __ldg(W.pad + x), z = __ldg(W.tim + x);
+                slots[row0 + k] = x;
+                if (k == 0) {
+                    m0y = y;
+                    m0z = z;
+                } else if (k == 1) {
+                    // state at the first hit with velocity m1 - m0, then the regular step to m1
+                    abg_init(fy, m0y, y);
+                    abg_init(fz, m0z, z);
+                    abg_predict(fy);
+                    abg_predict(fz);
+                    abg_update(fy, y);
+                    abg_update(fz, z);
+                } else {
+                    abg_predict(fy);
+                    abg_predict(fz);
+                    abg_update(fy, y);
+                    abg_update(fz, z);
+                }
+                if (k + 1 < len) x = W.up[x];
+            }
+            const int row_last = row0 + len - 1;
+            int r1, r0;
+            const int n_out = extend(W, g, fy, fz, rowbase, row_last, +1, slots, &r1);
+            // filter along the chain in descending rows
+            {
+                const int h1 = slots[row_last], h2 = slots[row_last - 1];
+                abg_init(fy, __ldg(W.pad + h1), __ldg(W.pad + h2));
+                abg_init(fz, __ldg(W.tim + h1), __ldg(W.tim + h2));
+                for (int k = len - 2; k >= 0; k--) {
+                    const int h = slots[row0 + k];
+                    abg_predict(fy);
+                    abg_predict(fz);
+                    abg_update(fy, __ldg(W.pad + h));
+                    abg_update(fz, __ldg(W.tim + h));
+                }
+            }
+            const int n_in = extend(W, g, fy, fz, rowbase, row0, -1, slots, &r0);
+            W.cand_n[t] = len + n_in + n_out;
+            W.cand_rows[t] = r0 | (r1 << 16);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_follow(const Work &W, cudaStream_t s) {
+    const int block = W.tune.block[3] > 0 ? W.tune.block[3] : 128;
+    const int grid = W.tune.grid[3] > 0 ? W.tune.grid[3] : W.sm_count * 8;
+    k_follow<<<grid, block, 0, s>>>(W);
+}
+
+}  // namespace tpc

@@ -1,0 +1,264 @@
+// S1 row-bin grid and S2 neighbour finding (cellular automaton, one decision per cluster;
+// arxiv 1712.09434 section 3).
+//
+// S1 (k_grid, one warp per (event, sector, row) bin): clusters of a bin are re-binned into 64 Z
+// slabs of 512 LSB by a stable counting sort, so that inside a slab they stay sorted by Y.  The
+// payload is packed (Y, Z) int32 plus the row-local index (uint16), stored from a 16-byte aligned
+// start pstart(bin), so a whole row can be moved into shared memory with one bulk-async (TMA)
+// copy.
+//
+// S2 (k_links, one CTA per bin, taken from a work queue): the CTA stages rows r-1 and r+1 into
+// shared memory with cp.async.bulk on an mbarrier (bounded wait), then every thread takes one
+// cluster c of row r and finds, among u on r+1 and d on r-1 inside the window |dY|, |dZ| <= W_LINK,
+// the pair of minimum (D, u, d), D = (Yu+Yd-2Yc)^2 + (Zu+Zd-2Zc)^2 <= D_MAX, all in integers.
+#include "tpc_common.cuh"
+
+namespace tpc {
+
+namespace {
+
+constexpr int LINK_STAGE_CAP = 4096;   // clusters of one row staged in shared memory
+
+__device__ __forceinline__ int warp_incl(int v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int slab_of(int z) { int s = z >> ZB_SHIFT; return s < NZB - 1 ? s : NZB - 1; }
+
+__global__ void __launch_bounds__(256) k_grid(Work W) {
+    __shared__ int hist[8][NZB];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    int *h = hist[wib];
+    for (int b = blockIdx.x * (blockDim.x >> 5) + wib; b < W.nbins; b += nw) {
+        const int c0 = W.bin_off[b], c1 = W.bin_off[b + 1];
+        const int cnt = c1 - c0;
+        if (cnt < 0 || cnt > 65535) {
+            if (lane == 0) set_status(W, ST_BOUNDS);
+            continue;
+        }
+        const int ps = pstart_of(c0, b);
+        h[lane] = 0;
+        h[lane + 32] = 0;
+        __syncwarp();
+        for (int i = lane; i < cnt; i += 32) atomicAdd(&h[slab_of(W.tim[c0 + i])], 1);
+        __syncwarp();
+        const int a0 = h[2 * lane], a1 = h[2 * lane + 1];
+        const int inc = warp_incl(a0 + a1);
+        const int ex = inc - a0 - a1;
+        __syncwarp();
+        h[2 * lane] = ex;
+        h[2 * lane + 1] = ex + a0;
+        uint16_t *zo = W.zoff + (size_t)b * ZOFF_STRIDE;
+        zo[2 * lane] = (uint16_t)ex;
+        zo[2 * lane + 1] = (uint16_t)(ex + a0);
+        if (lane == 31) zo[NZB] = (uint16_t)inc;
+        __syncwarp();
+        // stable scatter in chunks of 32, in cluster (= Y) order
+        for (int base = 0; base < cnt; base += 32) {
+            const int i = base + lane;
+            const bool v = i < cnt;
+            int y = 0, z = 0, s = NZB + lane;
+            if (v) {
+                y = W.pad[c0 + i];
+                z = W.tim[c0 + i];
+                s = slab_of(z);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, s);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int pos = v ? h[s] + rank : 0;
+            __syncwarp();
+            if (v && rank == 0) h[s] += __popc(peers);
+            __syncwarp();
+            if (v) {
+                W.gyz[ps + pos] = (int32_t)((uint32_t)(y & 0xffff) | ((uint32_t)z << 16));
+                W.gloc[ps + pos] = (uint16_t)i;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---- TMA bulk copy (global -> shared) on an mbarrier, with a bounded wait ---------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+struct RowView {
+    const int32_t *yz;        // packed (Y, Z) in slab order
+    const uint16_t *loc;      // row-local index
+    const uint16_t *zo;       // slab offsets [NZB + 1]
+};
+
+__device__ __forceinline__ int lower_y(const int32_t *yz, int lo, int hi, int y) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((int)(int16_t)(yz[mid] & 0xffff) < y) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) k_links(Work W) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    int32_t *s_yz[2] = {(int32_t *)smem, (int32_t *)(smem + LINK_STAGE_CAP * 4)};
+    uint16_t *s_loc[2] = {(uint16_t *)(smem + 2 * LINK_STAGE_CAP * 4),
+                          (uint16_t *)(smem + 2 * LINK_STAGE_CAP * 4 + LINK_STAGE_CAP * 2)};
+    __shared__ uint16_t s_zo[2][ZOFF_STRIDE + 1];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item;
+    const DevGeom &g = *W.geom;
+    const int nbe = g.n_sectors * g.n_rows;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    int32_t *q = W.counters + CNT_Q0 + 1;
+    for (int b = queue_next(q, 1, &s_item); b < W.nbins; b = queue_next(q, 1, &s_item)) {
+        const int r = (b % nbe) % g.n_rows;
+        const int c0 = W.bin_off[b], c1 = W.bin_off[b + 1];
+        if (r == 0 || r == g.n_rows - 1) {
+            for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) { W.up[c] = -1; W.down[c] = -1; }
+            continue;
+        }
+        RowView rv[2];
+        int nb[2], cb[2];
+        bool staged_any = false;
+        uint32_t tx = 0;
+        for (int k = 0; k < 2; k++) {
+            const int bb = k == 0 ? b - 1 : b + 1;          // 0: down row, 1: up row
+            cb[k] = W.bin_off[bb];
+            nb[k] = W.bin_off[bb + 1] - cb[k];
+            const int ps = pstart_of(cb[k], bb);
+            for (int i = threadIdx.x; i <= NZB; i += blockDim.x) s_zo[k][i] = W.zoff[(size_t)bb * ZOFF_STRIDE + i];
+            rv[k].zo = s_zo[k];
+            if (nb[k] > 0 && nb[k] <= LINK_STAGE_CAP) {
+                rv[k].yz = s_yz[k];
+                rv[k].loc = s_loc[k];
+                staged_any = true;
+                tx += ((nb[k] * 4 + 15) & ~15) + ((nb[k] * 2 + 15) & ~15);
+            } else {
+                rv[k].yz = W.gyz + ps;
+                rv[k].loc = W.gloc + ps;
+            }
+        }
+        if (staged_any && threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar, tx);
+            for (int k = 0; k < 2; k++) {
+                if (nb[k] > 0 && nb[k] <= LINK_STAGE_CAP) {
+                    const int bb = k == 0 ? b - 1 : b + 1;
+                    const int ps = pstart_of(cb[k], bb);
+                    bulk_g2s(s_yz[k], W.gyz + ps, (nb[k] * 4 + 15) & ~15, &bar);
+                    bulk_g2s(s_loc[k], W.gloc + ps, (nb[k] * 2 + 15) & ~15, &bar);
+                }
+            }
+        }
+        __syncthreads();
+        if (staged_any) {
+            const bool ok = mbar_wait(&bar, phase);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) set_status(W, ST_TIMEOUT);
+                mbar_wait(&bar, phase);   // give the copies in flight a second bounded chance
+                return;
+            }
+            phase ^= 1u;
+        }
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            const int yc = W.pad[c], zc = W.tim[c];
+            const int zl = slab_of(max(zc - W_LINK, 0)), zh = slab_of(zc + W_LINK);
+            unsigned long long best = ~0ull;
+            for (int su = zl; su <= zh; su++) {
+                const int hi = rv[1].zo[su + 1];
+                for (int iu = lower_y(rv[1].yz, rv[1].zo[su], hi, yc - W_LINK); iu < hi; iu++) {
+                    const int32_t vu = rv[1].yz[iu];
+                    const int yu = (int16_t)(vu & 0xffff);
+                    if (yu > yc + W_LINK) break;
+                    const int zu = (int)((uint32_t)vu >> 16);
+                    if (abs(zu - zc) > W_LINK) continue;
+                    const int lu = rv[1].loc[iu];
+                    for (int sd = zl; sd <= zh; sd++) {
+                        const int hd = rv[0].zo[sd + 1];
+                        for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
+                            const int32_t vd = rv[0].yz[id];
+                            const int yd = (int16_t)(vd & 0xffff);
+                            if (yd > yc + W_LINK) break;
+                            const int zd = (int)((uint32_t)vd >> 16);
+                            if (abs(zd - zc) > W_LINK) continue;
+                            const long long ey = yu + yd - 2 * yc, ez = zu + zd - 2 * zc;
+                            const long long D = ey * ey + ez * ez;
+                            if (D > D_MAX) continue;
+                            const unsigned long long key =
+                                ((unsigned long long)D << 32) | ((unsigned long long)lu << 16) | rv[0].loc[id];
+                            best = key < best ? key : best;
+                        }
+                    }
+                }
+            }
+            if (best != ~0ull) {
+                W.up[c] = cb[1] + (int)((best >> 16) & 0xffff);
+                W.down[c] = cb[0] + (int)(best & 0xffff);
+            } else {
+                W.up[c] = -1;
+                W.down[c] = -1;
+            }
+        }
+        __syncthreads();   // shared rows are overwritten by the next bin's copies
+    }
+}
+
+}  // namespace
+
+void launch_grid(const Work &W, cudaStream_t s) {
+    const int block = W.tune.block[0] > 0 ? W.tune.block[0] : 256;
+    const int warps = block / 32;
+    int grid = (W.nbins + warps - 1) / warps;
+    if (W.tune.grid[0] > 0 && grid > W.tune.grid[0]) grid = W.tune.grid[0];
+    if (grid < 1) grid = 1;
+    k_grid<<<grid, block, 0, s>>>(W);
+}
+
+void prepare_kernels() {
+    cudaFuncSetAttribute(k_links, cudaFuncAttributeMaxDynamicSharedMemorySize, LINK_STAGE_CAP * 12);
+}
+
+void launch_links(const Work &W, cudaStream_t s) {
+    const size_t smem = (size_t)LINK_STAGE_CAP * 12;
+    const int block = W.tune.block[1] > 0 ? W.tune.block[1] : 128;
+    int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 4;
+    if (grid > W.nbins) grid = W.nbins > 0 ? W.nbins : 1;
+    k_links<<<grid, block, smem, s>>>(W);
+}
+
+}  // namespace tpc

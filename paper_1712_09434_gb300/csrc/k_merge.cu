@@ -1,0 +1,255 @@
+// S7 inter-sector merging (arxiv 1712.09434 section 3: sectors are tracked independently and
+// concurrently, and the track segments are merged afterwards) and assembly of the output tracks.
+//
+// Ends: the first kept hit of a segment, and its outer end = last kept hit plus the kept hit
+// MERGE_BACK positions earlier, on integer (Xtab[row], Y, Z).  The outer end of S is rotated into
+// an adjacent sector of the same side with Q30 integer constants (floor shifts), extrapolated
+// linearly (floor division) to the row of T's first hit and compared there.  Every valid pair
+// offers (D, index) to both sides with 64-bit atomicMin; mutual bests are linked S -> T.  A chain
+// of links is one track; a cycle is cut in front of its smallest segment.  Track ids are an
+// exclusive scan of head flags in segment order (= seed order), so the output order is canonical.
+#include "tpc_common.cuh"
+
+namespace tpc {
+
+namespace {
+
+__device__ __forceinline__ uint32_t key_of(int n_rows, int n_hits, int local) {
+    return ((uint32_t)(n_rows - n_hits) << 23) | (uint32_t)local;
+}
+
+__device__ __forceinline__ int n_chains_of(const Work &W) {
+    const int n = W.counters[CNT_NCHAINS];
+    return n < W.cap_chains ? n : W.cap_chains;
+}
+
+// first candidate index of the (event, sector) of candidate t
+__device__ __forceinline__ int sector_base(const Work &W, int t) {
+    const int bin = W.chain_bin[t];
+    return W.chain_off[bin - bin % W.nr];
+}
+
+// ends of accepted segments; reset of the merge arrays
+__global__ void k_merge_ends(Work W) {
+    const DevGeom &g = *W.geom;
+    const int n = n_chains_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        W.bestT[t] = ~0ull;
+        W.bestS[t] = ~0ull;
+        W.next[t] = -1;
+        W.prev[t] = -1;
+        if (W.seg_n[t] < N_MIN) continue;
+        const uint32_t key = key_of(W.nr, W.cand_n[t], t - sector_base(W, t));
+        const int rr = W.cand_rows[t];
+        const int32_t *sl = W.cand_slots + (size_t)t * W.nr;
+        int ring_h[MERGE_BACK + 1], ring_r[MERGE_BACK + 1];
+        int first = -1, rf = 0, cnt = 0;
+        for (int r = rr & 0xffff; r <= (rr >> 16); r++) {
+            const int h = sl[r];
+            if (h < 0 || W.owner[h] != key) continue;
+            if (first < 0) { first = h; rf = r; }
+            ring_h[cnt % (MERGE_BACK + 1)] = h;
+            ring_r[cnt % (MERGE_BACK + 1)] = r;
+            cnt++;
+        }
+        if (cnt <= MERGE_BACK) { set_status(W, ST_BOUNDS); continue; }
+        const int sector = (W.chain_bin[t] % (W.ns * W.nr)) / W.nr;
+        const int iL = (cnt - 1) % (MERGE_BACK + 1), iB = (cnt - 1 - MERGE_BACK) % (MERGE_BACK + 1);
+        const int hL = ring_h[iL], rL = ring_r[iL], hB = ring_h[iB], rB = ring_r[iB];
+        W.inend[t] = make_int4(g.xtab[rf], W.pad[first], W.tim[first], sector);
+        atomicAdd(W.bin_cnt + (W.chain_bin[t] - W.chain_bin[t] % W.nr) + rf, 1);
+        W.outend[2 * t] = make_int4(g.xtab[rB], W.pad[hB], W.tim[hB], sector);
+        W.outend[2 * t + 1] = make_int4(g.xtab[rL], W.pad[hL], W.tim[hL], 0);
+    }
+}
+
+// Accepted segments listed per (event, sector, row of the first kept hit): the merge only looks at
+// segments whose first row lies inside the extrapolation reach.
+__global__ void k_merge_fill(Work W) {
+    const int n = n_chains_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        if (W.seg_n[t] < N_MIN) continue;
+        const int4 e = W.inend[t];
+        const int bin0 = W.chain_bin[t] - W.chain_bin[t] % W.nr;
+        int lo = 0, hi = W.nr - 1;   // row of the first kept hit from its Xtab value
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (W.geom->xtab[mid] < e.x) lo = mid + 1; else hi = mid;
+        }
+        const int b = bin0 + lo;
+        W.mrg_list[W.mrg_off[b] + atomicAdd(W.bin_cnt + b, 1)] = t;
+    }
+}
+
+__global__ void k_merge_match(Work W) {
+    const DevGeom &g = *W.geom;
+    const int n = n_chains_of(W);
+    const int half = W.ns / 2;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (W.seg_n[s] < N_MIN) continue;
+        const int4 p1 = W.outend[2 * s], p2 = W.outend[2 * s + 1];
+        const int ks = p1.w;
+        const int ev = W.chain_bin[s] / (W.ns * W.nr);
+        const int side0 = ks < half ? 0 : half;
+        unsigned long long best = ~0ull;
+        for (int k = 0; k < 2; k++) {
+            const int sgn = k == 0 ? +1 : -1;
+            const int kt = side0 + ((ks - side0) + (k == 0 ? 1 : half - 1)) % half;
+            if (k == 1 && kt == side0 + ((ks - side0) + 1) % half) break;   // tiny geometries
+            const long long X1 = p1.x, Y1 = p1.y, X2 = p2.x, Y2 = p2.y;
+            const long long x1 = (X1 * g.c30 + sgn * Y1 * g.s30) >> 30;
+            const long long y1 = (-sgn * X1 * g.s30 + Y1 * g.c30) >> 30;
+            const long long x2 = (X2 * g.c30 + sgn * Y2 * g.s30) >> 30;
+            const long long y2 = (-sgn * X2 * g.s30 + Y2 * g.c30) >> 30;
+            const long long dxs = x2 - x1;
+            if (dxs <= 0) continue;
+            const int b0 = (ev * W.ns + kt) * W.nr;
+            // rows whose plane is within MERGE_XMAX of the extrapolation start (one row of margin;
+            // the exact test is below)
+            const float pitch = (float)(g.xtab[W.nr - 1] - g.xtab[0]) / (float)(W.nr - 1);
+            int r_lo = (int)floorf((float)(x2 - MERGE_XMAX - g.xtab[0]) / pitch) - 1;
+            int r_hi = (int)ceilf((float)(x2 + MERGE_XMAX - g.xtab[0]) / pitch) + 1;
+            r_lo = max(r_lo, 0);
+            r_hi = min(r_hi, W.nr - 1);
+            if (r_lo > r_hi) continue;
+            const int i1 = W.mrg_off[b0 + r_hi + 1];
+            for (int i = W.mrg_off[b0 + r_lo]; i < i1; i++) {
+                const int t = W.mrg_list[i];
+                const int4 e = W.inend[t];
+                const long long XT = e.x;
+                const long long ax = XT - x2;
+                if ((ax < 0 ? -ax : ax) > MERGE_XMAX) continue;
+                const long long yp = y1 + floor_div((XT - x1) * (y2 - y1), dxs);
+                const long long zp = p1.z + floor_div((XT - x1) * (long long)(p2.z - p1.z), dxs);
+                const long long dy = e.y - yp, dz = e.z - zp;
+                if (dy > W_MERGE || dy < -W_MERGE || dz > W_MERGE || dz < -W_MERGE) continue;
+                const unsigned long long D = (unsigned long long)(dy * dy + dz * dz);
+                const unsigned long long kT = (D << 32) | (unsigned)t;
+                best = kT < best ? kT : best;
+                atomicMin(W.bestS + t, (D << 32) | (unsigned)s);
+            }
+        }
+        W.bestT[s] = best;
+    }
+}
+
+__global__ void k_merge_link(Work W) {
+    const int n = n_chains_of(W);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const unsigned long long v = W.bestT[s];
+        if (v == ~0ull) continue;
+        const int t = (int)(v & 0xffffffffu);
+        if (W.bestS[t] == ((v & 0xffffffff00000000ull) | (unsigned)s)) {
+            W.next[s] = t;
+            W.prev[t] = s;
+        }
+    }
+}
+
+__global__ void k_merge_heads(Work W) {
+    const int n = n_chains_of(W);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        int head = 0;
+        if (W.seg_n[s] >= N_MIN) {
+            if (W.prev[s] < 0) {
+                head = 1;
+            } else {
+                int x = W.prev[s], k = 0;
+                while (x >= 0 && x != s && k < MERGE_MAX_WALK) { x = W.prev[x]; k++; }
+                if (k >= MERGE_MAX_WALK) {
+                    set_status(W, ST_TIMEOUT);
+                } else if (x == s) {       // on a cycle: the smallest segment starts the track
+                    int m = s, y = W.next[s];
+                    k = 0;
+                    while (y != s && k < MERGE_MAX_WALK) { m = y < m ? y : m; y = W.next[y]; k++; }
+                    head = m == s;
+                }
+            }
+        }
+        W.head[s] = head;
+    }
+}
+
+// hits per track (walk the segment chain from its head)
+__global__ void k_track_count(Work W) {
+    const int n = n_chains_of(W);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (!W.head[s]) continue;
+        const int tid = W.head_id[s];
+        if (tid >= W.cap_tracks) { set_status(W, ST_CAPACITY); continue; }
+        int sum = 0, x = s, k = 0;
+        do {
+            sum += W.seg_n[x];
+            x = W.next[x];
+            k++;
+        } while (x >= 0 && !W.head[x] && k < MERGE_MAX_WALK);
+        W.trk_n[tid] = sum;
+        W.trk_head[tid] = s;
+    }
+}
+
+__global__ void k_track_write(Work W) {
+    const int nt = min(W.counters[CNT_NTRACKS], W.cap_tracks);
+    for (int tid = blockIdx.x * blockDim.x + threadIdx.x; tid < nt; tid += gridDim.x * blockDim.x) {
+        int pos = W.trk_off[tid];
+        int x = W.trk_head[tid], k = 0;
+        do {
+            const uint32_t key = key_of(W.nr, W.cand_n[x], x - sector_base(W, x));
+            const int rr = W.cand_rows[x];
+            const int32_t *sl = W.cand_slots + (size_t)x * W.nr;
+            const int sector = (W.chain_bin[x] % (W.ns * W.nr)) / W.nr;
+            for (int r = rr & 0xffff; r <= (rr >> 16); r++) {
+                const int h = sl[r];
+                if (h < 0 || W.owner[h] != key) continue;
+                if (pos < W.cap_hits) {
+                    W.trk_hits[pos] = h;
+                    W.label[h] = tid;
+                    W.trk_pack[2 * pos] = (int32_t)((uint32_t)(W.pad[h] & 0xffff) | ((uint32_t)W.tim[h] << 16));
+                    W.trk_pack[2 * pos + 1] = sector | (r << 16);
+                } else {
+                    set_status(W, ST_CAPACITY);
+                }
+                pos++;
+            }
+            x = W.next[x];
+            k++;
+        } while (x >= 0 && !W.head[x] && k < MERGE_MAX_WALK);
+    }
+}
+
+__global__ void k_event_offsets(Work W) {
+    const int n = n_chains_of(W);
+    const int nbe = W.ns * W.nr;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= W.n_events; e += gridDim.x * blockDim.x) {
+        if (e == W.n_events) {
+            W.ev_trk_off[e] = W.counters[CNT_NTRACKS];
+            *W.n_tracks = W.counters[CNT_NTRACKS];
+        } else {
+            W.ev_trk_off[e] = W.head_id[min(W.chain_off[e * nbe], n)];
+        }
+    }
+}
+
+}  // namespace
+
+void launch_merge(const Work &W, cudaStream_t s) {
+    const int block = W.tune.block[5] > 0 ? W.tune.block[5] : 128;
+    const int grid = W.tune.grid[5] > 0 ? W.tune.grid[5] : W.sm_count * 8;
+    cudaMemsetAsync(W.bin_cnt, 0, sizeof(int32_t) * (W.nbins + 1), s);
+    k_merge_ends<<<grid, block, 0, s>>>(W);
+    scan_exclusive(W.bin_cnt, W.mrg_off, W.nbins, nullptr, nullptr, W.scan_tmp, W.scan_tmp_len, s);
+    cudaMemsetAsync(W.bin_cnt, 0, sizeof(int32_t) * (W.nbins + 1), s);
+    k_merge_fill<<<grid, block, 0, s>>>(W);
+    k_merge_match<<<grid, block, 0, s>>>(W);
+    k_merge_link<<<grid, block, 0, s>>>(W);
+    k_merge_heads<<<grid, block, 0, s>>>(W);
+    scan_exclusive(W.head, W.head_id, W.cap_chains, W.counters + CNT_NCHAINS, W.counters + CNT_NTRACKS,
+                   W.scan_tmp, W.scan_tmp_len, s);
+    k_track_count<<<grid, block, 0, s>>>(W);
+    scan_exclusive(W.trk_n, W.trk_off, W.cap_tracks, W.counters + CNT_NTRACKS, W.counters + CNT_NHITS,
+                   W.scan_tmp, W.scan_tmp_len, s);
+    k_track_write<<<grid, block, 0, s>>>(W);
+    k_event_offsets<<<1, 128, 0, s>>>(W);
+}
+
+}  // namespace tpc

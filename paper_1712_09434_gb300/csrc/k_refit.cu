@@ -1,0 +1,439 @@
+// S0 cluster transformation, S8 Kalman-filter refit (FP32) and S9 its adjoint with FP64
+// cross-track reductions (arxiv 1712.09434 section 3: Kalman-filter fit and the final track
+// refit; sections 2 and 6: calibration of the cluster transformation fed back online).
+//
+// One thread per track (the paper's one-thread-per-track mapping).  The seed is the circle
+// through the first, middle and last hit at the nominal calibration, so it does not depend on
+// theta; the fit runs from the last hit to the first.  The adjoint stores the input state of every
+// K-th step (checkpoints) during the forward pass; the reverse sweep restores each checkpoint,
+// recomputes the K states of its segment and walks them backwards, so per-row states are
+// recomputed rather than stored for the whole track.  Per-track chi2 and gradient contributions
+// (s_vd, and (d_k, a_k) for every sector the track visits) are written as records and summed in
+// FP64 in a fixed order (deterministic).
+#include "kf.cuh"
+#include "tpc_common.cuh"
+
+namespace tpc {
+
+namespace {
+
+constexpr int CK_K = 8;            // steps between checkpoints
+constexpr int CK_WORDS = 25;       // x, p[5], P lower triangle[15], frame, rref, yref, zref
+constexpr int REC_SEC = 8;         // sector entries per track record
+constexpr int REC_WORDS = 2 + 3 * REC_SEC;
+constexpr int NPAR_MAX = 1 + 2 * MAX_SECTORS;
+constexpr int RED_T = 64;          // tracks per reduction block
+
+struct FitGeo {
+    kf::Geo<float> g;
+};
+
+// Kahan-Babuska compensated summation in FP32.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
+__device__ __forceinline__ void load_geo(const DevGeom &G, FitGeo &f) {
+    f.g.kB = G.kB;
+    f.g.sig2 = SIGMA2;
+    f.g.smax = SNP_MAX;
+    f.g.cmin = CPHI_MIN;
+    f.g.pitch = G.pitch;
+    f.g.half = G.half;
+    f.g.rot_c = G.rot_cos;
+    f.g.rot_s = G.rot_sin;
+    f.g.xr = G.xr;
+}
+
+struct HitRaw {
+    int k, r, Y, Z;
+};
+
+__device__ __forceinline__ HitRaw hit_raw(const Work &W, int i) {
+    const int2 v = reinterpret_cast<const int2 *>(W.trk_pack)[i];
+    HitRaw h;
+    h.Y = (int16_t)(v.x & 0xffff);
+    h.Z = (int)((uint32_t)v.x >> 16);
+    h.k = v.y & 0xffff;
+    h.r = (int)((uint32_t)v.y >> 16);
+    return h;
+}
+
+// S0: hit under theta (th[0] = s_vd, th[1+k] = d_k, th[1+ns+k] = a_k) as the filter sees it:
+// nominal coordinates (yn = Y*lsb, zn = side*(z_max - D), exact in FP32) plus the calibration
+// offsets xl = x_r*a_k*g', yc = y_raw*a_k*g', zc = side*(1 - s_vd)*D + d_k, with the derivative
+// factors dzc/ds_vd = -side*D and g' = (rho - x_first)/(span*rho).
+struct HitT {
+    kf::FHit<float> f;
+    float dzds, gp, xr, yraw;
+};
+
+__device__ __forceinline__ HitT transform(const DevGeom &G, const float *th, int ns, const HitRaw &h) {
+    HitT o;
+    const float side = h.k < G.half ? 1.f : -1.f;
+    o.xr = G.xr[h.r];
+    o.yraw = (float)h.Y * G.lsb;
+    const float D = (float)h.Z * G.lsb;
+    o.f.k = h.k;
+    o.f.r = h.r;
+    o.f.yn = o.yraw;
+    o.f.zn = side * (G.z_max - D);
+    o.f.zc = side * ((1.f - th[0]) * D) + th[1 + h.k];
+    o.dzds = -side * D;
+    const float rho = sqrtf(o.xr * o.xr + o.yraw * o.yraw);
+    o.gp = (rho - G.x_first) * G.inv_span / rho;
+    const float corr = th[1 + ns + h.k] * o.gp;
+    o.f.xl = o.xr * corr;
+    o.f.yc = o.yraw * corr;
+    return o;
+}
+
+// nominal hit, relative to the last hit E: (x - x_E, y) in E's frame
+__device__ __forceinline__ void nominal_rel(const DevGeom &G, const HitRaw &h, const HitRaw &e, float &x, float &y) {
+    const float yr = (float)h.Y * G.lsb;
+    if (h.k == e.k) {
+        x = (float)(h.r - e.r) * G.pitch;
+        y = yr;
+    } else {   // (x_e, y_e) = R(alpha_h - alpha_e) (x_h, y_h)
+        const int m = kf::rot_index(h.k, e.k, G.half);
+        const float c = G.rot_cos[m], s = G.rot_sin[m], xh = G.xr[h.r];
+        x = xh * c - yr * s - G.xr[e.r];
+        y = xh * s + yr * c;
+    }
+}
+__device__ __forceinline__ float nominal_z(const DevGeom &G, const HitRaw &h) {
+    const float side = h.k < G.half ? 1.f : -1.f;
+    return side * (G.z_max - (float)h.Z * G.lsb);
+}
+
+// Seed: sin phi, tan lambda, q/pT from the circle through the nominal first, middle and last hit
+// (theta-independent); position = the last hit under theta; references = the last hit.
+__device__ bool seed_track(const Work &W, const DevGeom &G, const float *th, int off, int n, kf::State<float> &s) {
+    const HitRaw e = hit_raw(W, off + n - 1), a = hit_raw(W, off), b = hit_raw(W, off + (n - 1) / 2);
+    float ax, ay, bx, by, ex, ey;
+    nominal_rel(G, a, e, ax, ay);
+    nominal_rel(G, b, e, bx, by);
+    nominal_rel(G, e, e, ex, ey);
+    const float ze = nominal_z(G, e);
+    if (!kf::seed3<float>(ax, ay, nominal_z(G, a) - ze, bx, by, ex, ey, 0.f, G.kB, SNP_MAX, s.p)) return false;
+    const HitT he = transform(G, th, W.ns, e);
+    s.p[0] = he.f.yc;
+    s.p[1] = he.f.zc;
+    s.x = he.f.xl;
+    s.rref = e.r;
+    s.yref = he.f.yn;
+    s.zref = he.f.zn;
+    s.frame = e.k;
+    const float c0[5] = {1.f, 1.f, 0.01f, 0.01f, 1.f};
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? c0[i] : 0.f;
+    return true;
+}
+
+__device__ __forceinline__ int n_tracks_of(const Work &W) {
+    const int n = W.counters[CNT_NTRACKS];
+    return n < W.cap_tracks ? n : W.cap_tracks;
+}
+
+// S8 at the nominal calibration: parameters, covariance, chi2, ndf of every track.
+__global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
+    __shared__ float th[NPAR_MAX];
+    const DevGeom &G = *W.geom;
+    const int ns = W.ns, np = 1 + 2 * ns;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) th[i] = theta[i];
+    __syncthreads();
+    FitGeo fg;
+    load_geo(G, fg);
+    const int nt = n_tracks_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int off = W.trk_off[t];
+        int n = W.trk_off[t + 1] - off;
+        if (off < 0 || n < 0 || off + n > W.cap_hits) {   // hits beyond the packed range: not fitted
+            set_status(W, ST_CAPACITY);
+            n = 0;
+        }
+        kf::State<float> s;
+        s.x = 0.f;
+        s.rref = 0;
+        s.frame = 0;
+        s.yref = s.zref = 0.f;
+        float chi2 = 0.f;
+        bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
+        for (int i = n - 1; ok && i >= 0; i--) {
+            const HitT m = transform(G, th, ns, hit_raw(W, off + i));
+            ok = kf::step_fwd(s, m.f, fg.g, chi2);
+        }
+        s.p[0] += s.yref;
+        s.p[1] += s.zref;
+        const float xabs = ok ? G.xr[s.rref] + s.x : 0.f;   // rref is valid only for a seeded track
+        for (int i = 0; i < 5; i++) W.par[5 * t + i] = ok ? s.p[i] : 0.f;
+        int m = 0;
+        for (int i = 0; i < 5; i++)
+            for (int j = 0; j <= i; j++) W.cov[15 * t + m++] = ok ? s.P[i][j] : 0.f;
+        W.xref[t] = ok ? xabs : 0.f;
+        W.chi2[t] = ok ? chi2 : 0.f;
+        W.ndf[t] = ok ? 2 * n - 5 : 0;
+    }
+}
+
+__device__ __forceinline__ void ck_store(float *dst, const kf::State<float> &s) {
+    dst[0] = s.x;
+    for (int i = 0; i < 5; i++) dst[1 + i] = s.p[i];
+    int m = 6;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) dst[m++] = s.P[i][j];
+    dst[21] = __int_as_float(s.frame);
+    dst[22] = __int_as_float(s.rref);
+    dst[23] = s.yref;
+    dst[24] = s.zref;
+}
+__device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
+    s.x = src[0];
+    for (int i = 0; i < 5; i++) s.p[i] = src[1 + i];
+    int m = 6;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            s.P[i][j] = src[m];
+            s.P[j][i] = src[m];
+            m++;
+        }
+    s.frame = __float_as_int(src[21]);
+    s.rref = __float_as_int(src[22]);
+    s.yref = src[23];
+    s.zref = src[24];
+}
+
+// S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
+template <bool GRAD>
+__global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta, const float *weight, float *ck,
+                                                    float *rec) {
+    __shared__ float th[NPAR_MAX];
+    const DevGeom &G = *W.geom;
+    const int ns = W.ns, np = 1 + 2 * ns;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) th[i] = (float)theta[i];
+    __syncthreads();
+    FitGeo fg;
+    load_geo(G, fg);
+    const int nt = n_tracks_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int off = W.trk_off[t];
+        int n = W.trk_off[t + 1] - off;
+        if (off < 0 || n < 0 || off + n > W.cap_hits) {
+            set_status(W, ST_CAPACITY);
+            n = 0;
+        }
+        float *r = rec + (size_t)t * REC_WORDS;
+        const float w = weight ? weight[t] : 1.f;
+        if (w == 0.f) n = 0;   // excluded track: no fit, no adjoint
+        float *ckt = ck + ((size_t)(off / CK_K) + t) * CK_WORDS;
+        kf::State<float> s;
+        s.x = 0.f;
+        s.rref = 0;
+        s.frame = 0;
+        s.yref = s.zref = 0.f;
+        float chi2 = 0.f;
+        bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
+        for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q
+            if (GRAD && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
+            const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q));
+            ok = kf::step_fwd(s, m.f, fg.g, chi2);
+        }
+        r[0] = ok ? w * chi2 : 0.f;
+        r[1] = 0.f;
+        for (int k = 0; k < REC_SEC; k++) {
+            r[2 + 3 * k] = __int_as_float(-1);
+            r[3 + 3 * k] = 0.f;
+            r[4 + 3 * k] = 0.f;
+        }
+        if (!GRAD || !ok) continue;
+        // reverse sweep, segment by segment from the last checkpoint
+        kf::Adj<float> a;
+        kf::adj_zero(a);
+        Kahan gs, gd, ga;       // compensated FP32 sums over the hits of the track
+        int cur_sec = -1, n_ent = 0;
+        float ent_d[REC_SEC], ent_a[REC_SEC];
+        int ent_s[REC_SEC];
+        kf::State<float> buf[CK_K];
+        for (int q0 = ((n - 1) / CK_K) * CK_K; q0 >= 0; q0 -= CK_K) {
+            const int q1 = min(q0 + CK_K, n);
+            kf::State<float> st;
+            ck_load(ckt + (q0 / CK_K) * CK_WORDS, st);
+            float dummy = 0.f;
+            for (int q = q0; q < q1; q++) {
+                buf[q - q0] = st;
+                const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q));
+                kf::step_fwd(st, m.f, fg.g, dummy);
+            }
+            for (int q = q1 - 1; q >= q0; q--) {
+                const HitRaw h = hit_raw(W, off + n - 1 - q);
+                const HitT m = transform(G, th, ns, h);
+                float xb = 0.f, yb = 0.f, zb = 0.f;
+                kf::step_bwd(buf[q - q0], m.f, fg.g, a, &xb, &yb, &zb);
+                if (q == 0) {   // the seed position is this hit's (x, y, z)
+                    xb += a.x;
+                    yb += a.p[0];
+                    zb += a.p[1];
+                }
+                // chain rule through S0
+                if (h.k != cur_sec) {
+                    if (cur_sec >= 0) {
+                        if (n_ent < REC_SEC) {
+                            ent_s[n_ent] = cur_sec;
+                            ent_d[n_ent] = gd.value();
+                            ent_a[n_ent] = ga.value();
+                        } else {
+                            set_status(W, ST_CAPACITY);
+                        }
+                        n_ent++;
+                    }
+                    cur_sec = h.k;
+                    gd = Kahan();
+                    ga = Kahan();
+                }
+                gs.add(zb * m.dzds);
+                gd.add(zb);
+                ga.add((xb * m.xr + yb * m.yraw) * m.gp);
+            }
+        }
+        if (cur_sec >= 0) {
+            if (n_ent < REC_SEC) {
+                ent_s[n_ent] = cur_sec;
+                ent_d[n_ent] = gd.value();
+                ent_a[n_ent] = ga.value();
+            } else {
+                set_status(W, ST_CAPACITY);
+            }
+            n_ent++;
+        }
+        // A common shift of every z of the track (hits and seed) leaves its chi2 unchanged, so the
+        // exact d/dd_k contributions of one track sum to zero.  Project the FP32 sums onto that
+        // constraint (equal share of the rounding residual to every entry): a single-sector track
+        // contributes exactly zero.
+        const int ne = n_ent < REC_SEC ? n_ent : REC_SEC;
+        Kahan tot;
+        for (int k = 0; k < ne; k++) tot.add(ent_d[k]);
+        const float share = ne > 0 ? tot.value() / (float)ne : 0.f;
+        for (int k = 0; k < ne; k++) {
+            r[2 + 3 * k] = __int_as_float(ent_s[k]);
+            r[3 + 3 * k] = w * (ne == 1 ? 0.f : ent_d[k] - share);
+            r[4 + 3 * k] = w * ent_a[k];
+        }
+        r[1] = w * gs.value();
+    }
+}
+
+// Deterministic FP64 reduction of the track records: block b sums tracks [b*RED_T, (b+1)*RED_T)
+// column by column in track order into part[b][np + 1] (column np = chi2); blocks past the last
+// track exit at once.
+__global__ void __launch_bounds__(RED_T) k_reduce_records(Work W, const float *rec, double *part) {
+    __shared__ float m[RED_T][NPAR_MAX + 1];
+    const int ns = W.ns, np = 1 + 2 * ns;
+    const int nt = n_tracks_of(W);
+    if ((long long)blockIdx.x * RED_T >= nt) return;
+    const int t = blockIdx.x * RED_T + threadIdx.x;
+    for (int j = 0; j <= np; j++) m[threadIdx.x][j] = 0.f;
+    if (t < nt) {
+        const float *r = rec + (size_t)t * REC_WORDS;
+        m[threadIdx.x][np] = r[0];
+        m[threadIdx.x][0] = r[1];
+        for (int k = 0; k < REC_SEC; k++) {
+            const int sec = __float_as_int(r[2 + 3 * k]);
+            if (sec < 0 || sec >= ns) continue;
+            m[threadIdx.x][1 + sec] += r[3 + 3 * k];
+            m[threadIdx.x][1 + ns + sec] += r[4 + 3 * k];
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= np; j += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < RED_T; i++) acc += (double)m[i][j];
+        part[(size_t)blockIdx.x * (np + 1) + j] = acc;
+    }
+}
+
+// Sum of the block partials: one warp per column, lane l takes blocks l, l+32, ... in order and
+// the lanes combine with a fixed butterfly, so the result does not depend on timing.
+__global__ void k_reduce_final(Work W, int np, const double *part, double *sum_chi2, double *grad) {
+    const int nt = n_tracks_of(W);
+    const int nb = (nt + RED_T - 1) / RED_T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j <= np; j += nw) {
+        double acc = 0.0;
+        for (int b = lane; b < nb; b += 32) acc += part[(size_t)b * (np + 1) + j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            if (j == np) *sum_chi2 = acc;
+            else if (grad) grad[j] = acc;
+        }
+    }
+}
+
+// Hit list of caller-provided tracks -> packed (Y, Z, sector, row) per hit; the bin of a cluster is
+// found by binary search in bin_off.
+__global__ void k_pack_hits(Work W) {
+    const int nt = n_tracks_of(W);
+    int nh = W.trk_off[nt];
+    if (nh > W.cap_hits || nh < 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(W, ST_CAPACITY);
+        nh = nh < 0 ? 0 : W.cap_hits;
+    }
+    const int nbe = W.ns * W.nr;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += gridDim.x * blockDim.x) {
+        const int h = W.trk_hits[i];
+        if (h < 0 || h >= W.n_clusters) {
+            set_status(W, ST_BOUNDS);
+            W.trk_pack[2 * i] = 0;
+            W.trk_pack[2 * i + 1] = 0;
+            continue;
+        }
+        int lo = 0, hi = W.nbins;   // last b with bin_off[b] <= h
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (W.bin_off[mid] <= h) lo = mid; else hi = mid;
+        }
+        const int sector = (lo % nbe) / W.nr, row = lo % W.nr;
+        W.trk_pack[2 * i] = (int32_t)((uint32_t)(W.pad[h] & 0xffff) | ((uint32_t)W.tim[h] << 16));
+        W.trk_pack[2 * i + 1] = sector | (row << 16);
+    }
+}
+
+}  // namespace
+
+void launch_pack_hits(const Work &W, cudaStream_t s) { k_pack_hits<<<W.sm_count * 4, 256, 0, s>>>(W); }
+
+int refit_ck_words(int cap_hits, int cap_tracks) { return (cap_hits / CK_K + cap_tracks + 1) * CK_WORDS; }
+int refit_rec_words(int cap_tracks) { return cap_tracks * REC_WORDS; }
+int refit_part_doubles(int cap_tracks, int ns) { return ((cap_tracks + RED_T - 1) / RED_T + 1) * (2 * ns + 2); }
+
+
+void launch_refit(const Work &W, const float *theta, cudaStream_t s) {
+    const int block = W.tune.block[6] > 0 ? W.tune.block[6] : 128;
+    const int grid = W.tune.grid[6] > 0 ? W.tune.grid[6] : W.sm_count * 8;
+    k_refit<<<grid, block, 0, s>>>(W, theta);
+}
+
+void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, bool grad, float *ck, float *rec,
+                           cudaStream_t s) {
+    const int block = W.tune.block[7] > 0 ? W.tune.block[7] : 128;
+    const int grid = W.tune.grid[7] > 0 ? W.tune.grid[7] : W.sm_count * 8;
+    if (grad)
+        k_refit_grad<true><<<grid, block, 0, s>>>(W, theta, weight, ck, rec);
+    else
+        k_refit_grad<false><<<grid, block, 0, s>>>(W, theta, weight, ck, rec);
+}
+
+void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,
+                              cudaStream_t s) {
+    const int cap = W.cap_tracks < W.cap_chains ? W.cap_tracks : W.cap_chains;
+    const int nb = (cap + RED_T - 1) / RED_T;
+    k_reduce_records<<<nb > 0 ? nb : 1, RED_T, 0, s>>>(W, rec, part);
+    k_reduce_final<<<1, 1024, 0, s>>>(W, 1 + 2 * W.ns, part, sum_chi2, grad);
+}
+
+}  // namespace tpc

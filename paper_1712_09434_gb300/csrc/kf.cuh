@@ -1,0 +1,638 @@
+// Kalman-filter helix refit and its hand-written adjoint (arxiv 1712.09434 section 3: Kalman
+// filter track fitting; the final track refit of the merger).  Header-only, templated on the
+// scalar type; the library instantiates it in float.
+//
+// State (y, z, sin phi, tan lambda, q/pT) at local x in the frame of the current hit's sector;
+// covariance P (symmetric 5x5, kept as a full matrix in registers).  One step =
+//   rotation into the hit's sector if it changed (reference surface moved with the point),
+//   exact helix propagation to the hit's x (C = kB q/pT; sin phi2 = sin phi + C dx;
+//     dy = dx T, T = (sin phi + sin phi2)/(cos phi + cos phi2); L = dx sqrt(1+T^2);
+//     dz = tan lambda * L * asin(C L/2)/(C L/2)), covariance F P F^T with the step Jacobian,
+//   measurement update with (y, z), R = diag(s2, s2), symmetric form P - U S^-1 U^T.
+//
+// The adjoint propagates d(sum chi2)/d(.) backwards through one step.  Matrix adjoints use the
+// symmetric-gradient convention: for a symmetric argument P, Pb is symmetric and
+// d f = sum_ij Pb_ij dP_ij.
+#pragma once
+
+#include <math.h>
+
+#if defined(__CUDACC__)
+#define KF_HD __host__ __device__ __forceinline__
+#else
+#define KF_HD inline
+#endif
+
+namespace kf {
+
+KF_HD float k_sqrt(float a) { return sqrtf(a); }
+KF_HD double k_sqrt(double a) { return sqrt(a); }
+KF_HD float k_asin(float a) { return asinf(a); }
+KF_HD double k_asin(double a) { return asin(a); }
+KF_HD float k_abs(float a) { return fabsf(a); }
+KF_HD double k_abs(double a) { return fabs(a); }
+KF_HD float k_fma(float a, float b, float c) { return fmaf(a, b, c); }
+KF_HD double k_fma(double a, double b, double c) { return fma(a, b, c); }
+
+// asin(u)/u and its derivative; power series for small |u| (coefficients of the Taylor series of
+// asin(u)/u = sum (2k)!/(4^k (k!)^2 (2k+1)) u^(2k)).
+template <class T>
+KF_HD T asinc(T u) {
+    const T u2 = u * u;
+    if (k_abs(u) < T(0.25))
+        return T(1) + u2 * (T(1.0 / 6) + u2 * (T(3.0 / 40) + u2 * (T(5.0 / 112) + u2 * (T(35.0 / 1152) +
+               u2 * (T(63.0 / 2816) + u2 * T(231.0 / 13312))))));
+    return k_asin(u) / u;
+}
+template <class T>
+KF_HD T asinc_d(T u) {
+    const T u2 = u * u;
+    if (k_abs(u) < T(0.25))
+        return u * (T(2.0 / 6) + u2 * (T(12.0 / 40) + u2 * (T(30.0 / 112) + u2 * (T(8 * 35.0 / 1152) +
+               u2 * (T(10 * 63.0 / 2816) + u2 * T(12 * 231.0 / 13312))))));
+    return (u / k_sqrt(T(1) - u2) - k_asin(u)) / u2;
+}
+
+// Positions are kept relative to the nominal coordinates of a reference hit (the last hit
+// processed): absolute x = xr[rref] + x, y = yref + p[0], z = zref + p[1].  Nominal coordinates
+// are exact in FP32 (row planes, multiples of the fixed-point unit), so the state carries only
+// small offsets of the size of a residual and the FP32 rounding of absolute coordinates up to
+// 250 cm never enters the filter.  The references are calibration-independent constants: they
+// move the origin, not the function, so derivatives are unchanged.
+template <class T>
+struct State {
+    T x;
+    T p[5];
+    T P[5][5];
+    int frame;
+    int rref;
+    T yref, zref;
+};
+
+template <class T>
+struct Adj {
+    T x;
+    T p[5];
+    T G[5][5];
+};
+
+template <class T>
+KF_HD void adj_zero(Adj<T> &a) {
+    a.x = T(0);
+    for (int i = 0; i < 5; i++) {
+        a.p[i] = T(0);
+        for (int j = 0; j < 5; j++) a.G[i][j] = T(0);
+    }
+}
+
+// ---- sector rotation --------------------------------------------------------------------------
+// Rotate by da (cos ca, sin sa) into the new frame.  Returns false if cos phi' <= cmin.
+template <class T>
+KF_HD bool rot_fwd(State<T> &s, T ca, T sa, T kB, T cmin) {
+    const T sn = s.p[2];
+    const T cs = k_sqrt(T(1) - sn * sn);
+    const T x1 = s.x * ca + s.p[0] * sa;
+    const T y1 = -s.x * sa + s.p[0] * ca;
+    const T sn1 = sn * ca - cs * sa;
+    const T cs1 = cs * ca + sn * sa;
+    if (!(cs1 > cmin)) return false;
+    const T C = kB * s.p[4];
+    const T j00 = cs / cs1, j10 = -s.p[3] * sa / cs1, j20 = -C * sa, j22 = cs1 / cs;
+    // P <- J P J^T, J = I except rows 0,1,2 / column 0 and (2,2)
+    T A[5][5];
+    for (int j = 0; j < 5; j++) {
+        A[0][j] = j00 * s.P[0][j];
+        A[1][j] = j10 * s.P[0][j] + s.P[1][j];
+        A[2][j] = j20 * s.P[0][j] + j22 * s.P[2][j];
+        A[3][j] = s.P[3][j];
+        A[4][j] = s.P[4][j];
+    }
+    for (int i = 0; i < 5; i++) {
+        s.P[i][0] = j00 * A[i][0];
+        s.P[i][1] = j10 * A[i][0] + A[i][1];
+        s.P[i][2] = j20 * A[i][0] + j22 * A[i][2];
+        s.P[i][3] = A[i][3];
+        s.P[i][4] = A[i][4];
+    }
+    s.x = x1;
+    s.p[0] = y1;
+    s.p[2] = sn1;
+    return true;
+}
+
+// Adjoint of rot_fwd.  `s` is the state BEFORE the rotation; a holds the adjoint of the state
+// after it and is overwritten with the adjoint of the state before it.
+template <class T>
+KF_HD void rot_bwd(const State<T> &s, T ca, T sa, T kB, Adj<T> &a) {
+    const T sn = s.p[2], tl = s.p[3], q = s.p[4];
+    const T cs = k_sqrt(T(1) - sn * sn);
+    const T cs1 = cs * ca + sn * sa;
+    const T ic1 = T(1) / cs1;
+    const T C = kB * q;
+    const T j00 = cs * ic1, j10 = -tl * sa * ic1, j20 = -C * sa, j22 = cs1 / cs;
+    // Jb = 2 G' J P at the state-dependent entries (0,0), (1,0), (2,0), (2,2)
+    T GJ[5][5];   // G' J
+    for (int i = 0; i < 5; i++) {
+        GJ[i][0] = a.G[i][0] * j00 + a.G[i][1] * j10 + a.G[i][2] * j20;
+        GJ[i][1] = a.G[i][1];
+        GJ[i][2] = a.G[i][2] * j22;
+        GJ[i][3] = a.G[i][3];
+        GJ[i][4] = a.G[i][4];
+    }
+    T Jb00 = T(0), Jb10 = T(0), Jb20 = T(0), Jb22 = T(0);
+    for (int k = 0; k < 5; k++) {
+        Jb00 += GJ[0][k] * s.P[k][0];
+        Jb10 += GJ[1][k] * s.P[k][0];
+        Jb20 += GJ[2][k] * s.P[k][0];
+        Jb22 += GJ[2][k] * s.P[k][2];
+    }
+    Jb00 *= T(2);
+    Jb10 *= T(2);
+    Jb20 *= T(2);
+    Jb22 *= T(2);
+    // G <- J^T G' J
+    for (int j = 0; j < 5; j++) {
+        const T r0 = j00 * GJ[0][j] + j10 * GJ[1][j] + j20 * GJ[2][j];
+        const T r2 = j22 * GJ[2][j];
+        a.G[0][j] = r0;
+        a.G[1][j] = GJ[1][j];
+        a.G[2][j] = r2;
+        a.G[3][j] = GJ[3][j];
+        a.G[4][j] = GJ[4][j];
+    }
+    // state: x1 = x ca + y sa, y1 = -x sa + y ca, sn1 = sn ca - cs sa, (z, tl, q) unchanged,
+    // plus the Jacobian entries' dependence on (sn, tl, q).
+    T xb = a.x * ca - a.p[0] * sa;
+    T yb = a.x * sa + a.p[0] * ca;
+    T snb = a.p[2] * ca;
+    T csb = -a.p[2] * sa;
+    T tlb = a.p[3];
+    T qb = a.p[4];
+    T zb = a.p[1];
+    // j00 = cs ic1 ; j10 = -tl sa ic1 ; j20 = -C sa ; j22 = cs1 / cs
+    T ic1b = Jb00 * cs - Jb10 * tl * sa;
+    csb += Jb00 * ic1 - Jb22 * cs1 / (cs * cs);
+    tlb += -Jb10 * sa * ic1;
+    T Cb = -Jb20 * sa;
+    T cs1b = Jb22 / cs - ic1b * ic1 * ic1;
+    // cs1 = cs ca + sn sa
+    csb += cs1b * ca;
+    snb += cs1b * sa;
+    // cs = sqrt(1 - sn^2)
+    snb += -csb * sn / cs;
+    qb += Cb * kB;
+    a.x = xb;
+    a.p[0] = yb;
+    a.p[1] = zb;
+    a.p[2] = snb;
+    a.p[3] = tlb;
+    a.p[4] = qb;
+}
+
+// ---- helix propagation ------------------------------------------------------------------------
+template <class T>
+struct PropV {   // forward intermediates of one propagation step
+    T dx, C, s2, c1, c2, ic1, ic2, den, T_, W, sW, L, u, f, arc, h, g2;
+    T F02, F04, F12, F13, F14, F24;
+};
+
+template <class T>
+KF_HD bool prop_vals(const State<T> &s, T dx, T kB, T smax, PropV<T> &v) {
+    const T sn = s.p[2], tl = s.p[3], q = s.p[4];
+    v.dx = dx;
+    v.C = kB * q;
+    v.s2 = sn + v.C * v.dx;
+    if (!(k_abs(v.s2) < smax) || !(k_abs(sn) < smax)) return false;
+    v.c1 = k_sqrt(T(1) - sn * sn);
+    v.c2 = k_sqrt(T(1) - v.s2 * v.s2);
+    v.ic1 = T(1) / v.c1;
+    v.ic2 = T(1) / v.c2;
+    v.den = v.c1 + v.c2;
+    v.T_ = (sn + v.s2) / v.den;
+    v.W = T(1) + v.T_ * v.T_;
+    v.sW = k_sqrt(v.W);
+    v.L = v.dx * v.sW;
+    v.u = T(0.5) * v.C * v.L;
+    v.f = asinc(v.u);
+    v.arc = v.L * v.f;
+    v.h = T(0.5) * (v.ic1 + v.ic2);
+    v.g2 = T(0.5) * v.ic2 * kB * v.dx * v.dx;
+    v.F02 = v.dx * v.W * v.h;
+    v.F04 = v.W * v.g2;
+    v.F12 = tl * v.dx * v.T_ * v.sW * v.h;
+    v.F13 = v.arc;
+    v.F14 = tl * v.T_ * v.sW * v.g2;
+    v.F24 = kB * v.dx;
+    return true;
+}
+
+// Propagate by dx along the helix and move the (y, z) origin by (dyref, dzref) (the caller updates
+// the reference x).
+template <class T>
+KF_HD bool prop_fwd(State<T> &s, T dx, T kB, T smax, T dyref = T(0), T dzref = T(0)) {
+    PropV<T> v;
+    if (!prop_vals(s, dx, kB, smax, v)) return false;
+    const T a = v.F02, b = v.F04, c = v.F12, d = v.F13, e = v.F14, f = v.F24;
+    T A[5][5];
+    for (int j = 0; j < 5; j++) {
+        A[0][j] = s.P[0][j] + a * s.P[2][j] + b * s.P[4][j];
+        A[1][j] = s.P[1][j] + c * s.P[2][j] + d * s.P[3][j] + e * s.P[4][j];
+        A[2][j] = s.P[2][j] + f * s.P[4][j];
+        A[3][j] = s.P[3][j];
+        A[4][j] = s.P[4][j];
+    }
+    for (int i = 0; i < 5; i++) {
+        s.P[i][0] = A[i][0] + a * A[i][2] + b * A[i][4];
+        s.P[i][1] = A[i][1] + c * A[i][2] + d * A[i][3] + e * A[i][4];
+        s.P[i][2] = A[i][2] + f * A[i][4];
+        s.P[i][3] = A[i][3];
+        s.P[i][4] = A[i][4];
+    }
+    s.p[0] += v.dx * v.T_ - dyref;
+    s.p[1] += s.p[3] * v.arc - dzref;
+    s.p[2] = v.s2;
+    return true;
+}
+
+// Adjoint of prop_fwd; `s` is the state before the step.  Returns the adjoint of dx (a.x, the
+// adjoint of the reference x, is left to the caller).
+template <class T>
+KF_HD T prop_bwd(const State<T> &s, T dx, T kB, T smax, Adj<T> &a) {
+    PropV<T> v;
+    prop_vals(s, dx, kB, smax, v);
+    const T sn = s.p[2], tl = s.p[3];
+    T F[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) F[i][j] = i == j ? T(1) : T(0);
+    F[0][2] = v.F02; F[0][4] = v.F04; F[1][2] = v.F12; F[1][3] = v.F13; F[1][4] = v.F14; F[2][4] = v.F24;
+    // Fb = 2 G' F P at the six state-dependent entries
+    T GF[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            T acc = T(0);
+            for (int k = 0; k < 5; k++) acc += a.G[i][k] * F[k][j];
+            GF[i][j] = acc;
+        }
+    T Fb[5][5];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 5; j++) {
+            T acc = T(0);
+            for (int k = 0; k < 5; k++) acc += GF[i][k] * s.P[k][j];
+            Fb[i][j] = T(2) * acc;
+        }
+    // G <- F^T G' F
+    T Gn[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) {
+            T acc = T(0);
+            for (int k = 0; k < 5; k++) acc += F[k][i] * GF[k][j];
+            Gn[i][j] = acc;
+        }
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) a.G[i][j] = Gn[i][j];
+    const T F02b = Fb[0][2], F04b = Fb[0][4], F12b = Fb[1][2], F13b = Fb[1][3], F14b = Fb[1][4], F24b = Fb[2][4];
+    // state outputs: y' = y + dx T, z' = z + tl arc, s' = s2, tl' = tl, q' = q, x' = xh
+    const T ypb = a.p[0], zpb = a.p[1], spb = a.p[2];
+    T yb = ypb, zb = zpb, tlb = a.p[3], qb = a.p[4];
+    T dxb = T(0), Tb = T(0), arcb = T(0), s2b = spb, snb = T(0);
+    // Jacobian entries
+    arcb += F13b;
+    // F14 = tl T sW g2
+    tlb += F14b * v.T_ * v.sW * v.g2;
+    Tb += F14b * tl * v.sW * v.g2;
+    T sWb = F14b * tl * v.T_ * v.g2;
+    T g2b = F14b * tl * v.T_ * v.sW;
+    // F12 = tl dx T sW h
+    tlb += F12b * v.dx * v.T_ * v.sW * v.h;
+    dxb += F12b * tl * v.T_ * v.sW * v.h;
+    Tb += F12b * tl * v.dx * v.sW * v.h;
+    sWb += F12b * tl * v.dx * v.T_ * v.h;
+    T hb = F12b * tl * v.dx * v.T_ * v.sW;
+    // F04 = W g2
+    T Wb = F04b * v.g2;
+    g2b += F04b * v.W;
+    // F02 = dx W h
+    dxb += F02b * v.W * v.h;
+    Wb += F02b * v.dx * v.h;
+    hb += F02b * v.dx * v.W;
+    // F24 = kB dx
+    dxb += F24b * kB;
+    // g2 = 0.5 ic2 kB dx^2
+    T ic2b = g2b * T(0.5) * kB * v.dx * v.dx;
+    dxb += g2b * v.ic2 * kB * v.dx;
+    // h = 0.5 (ic1 + ic2)
+    T ic1b = T(0.5) * hb;
+    ic2b += T(0.5) * hb;
+    // state part
+    T dyb = ypb;                 // y' = y + dy, dy = dx T
+    tlb += zpb * v.arc;          // z' = z + tl arc
+    arcb += zpb * tl;
+    // arc = L f
+    T Lb = arcb * v.f;
+    T fb = arcb * v.L;
+    // f = asinc(u)
+    T ub = fb * asinc_d(v.u);
+    // u = 0.5 C L
+    T Cb = ub * T(0.5) * v.L;
+    Lb += ub * T(0.5) * v.C;
+    // L = dx sW
+    dxb += Lb * v.sW;
+    sWb += Lb * v.dx;
+    // sW = sqrt(W)
+    Wb += sWb * T(0.5) / v.sW;
+    // W = 1 + T^2
+    Tb += Wb * T(2) * v.T_;
+    // dy = dx T
+    dxb += dyb * v.T_;
+    Tb += dyb * v.dx;
+    // T = (sn + s2) / den
+    const T numb = Tb / v.den;
+    const T denb = -Tb * v.T_ / v.den;
+    snb += numb;
+    s2b += numb;
+    T c1b = denb, c2b = denb;
+    // ic = 1/c
+    c1b += -ic1b * v.ic1 * v.ic1;
+    c2b += -ic2b * v.ic2 * v.ic2;
+    // c = sqrt(1 - s^2)
+    snb += -c1b * sn * v.ic1;
+    s2b += -c2b * v.s2 * v.ic2;
+    // s2 = sn + C dx
+    snb += s2b;
+    Cb += s2b * v.dx;
+    dxb += s2b * v.C;
+    // C = kB q
+    qb += Cb * kB;
+    a.p[0] = yb;
+    a.p[1] = zb;
+    a.p[2] = snb;
+    a.p[3] = tlb;
+    a.p[4] = qb;
+    return dxb;
+}
+
+// ---- measurement update ----------------------------------------------------------------------
+template <class T>
+KF_HD T upd_fwd(State<T> &s, T ym, T zm, T s2) {
+    const T r0 = ym - s.p[0], r1 = zm - s.p[1];
+    const T S00 = s.P[0][0] + s2, S01 = s.P[0][1], S11 = s.P[1][1] + s2;
+    const T idet = T(1) / (S00 * S11 - S01 * S01);
+    const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
+    const T chi2 = r0 * r0 * i00 + T(2) * r0 * r1 * i01 + r1 * r1 * i11;
+    T U0[5], U1[5], K0[5], K1[5];
+    for (int j = 0; j < 5; j++) {
+        U0[j] = s.P[j][0];
+        U1[j] = s.P[j][1];
+        K0[j] = U0[j] * i00 + U1[j] * i01;
+        K1[j] = U0[j] * i01 + U1[j] * i11;
+    }
+    for (int j = 0; j < 5; j++) s.p[j] += K0[j] * r0 + K1[j] * r1;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            const T v = s.P[i][j] - (K0[i] * U0[j] + K1[i] * U1[j]);
+            s.P[i][j] = v;
+            s.P[j][i] = v;
+        }
+    return chi2;
+}
+
+// Adjoint of upd_fwd with d(chi2) = 1; `s` is the state before the update.  Writes the adjoint
+// of the measurement to (*ymb, *zmb).
+template <class T>
+KF_HD void upd_bwd(const State<T> &s, T ym, T zm, T s2, Adj<T> &a, T *ymb, T *zmb) {
+    const T r0 = ym - s.p[0], r1 = zm - s.p[1];
+    const T S00 = s.P[0][0] + s2, S01 = s.P[0][1], S11 = s.P[1][1] + s2;
+    const T idet = T(1) / (S00 * S11 - S01 * S01);
+    const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
+    T U[5][2], K[5][2];
+    for (int j = 0; j < 5; j++) {
+        U[j][0] = s.P[j][0];
+        U[j][1] = s.P[j][1];
+        K[j][0] = U[j][0] * i00 + U[j][1] * i01;
+        K[j][1] = U[j][0] * i01 + U[j][1] * i11;
+    }
+    // rb = K^T pb + 2 Si r
+    T rb0 = T(2) * (i00 * r0 + i01 * r1), rb1 = T(2) * (i01 * r0 + i11 * r1);
+    for (int j = 0; j < 5; j++) {
+        rb0 += K[j][0] * a.p[j];
+        rb1 += K[j][1] * a.p[j];
+    }
+    // Kb = pb r^T
+    T Kb[5][2];
+    for (int j = 0; j < 5; j++) {
+        Kb[j][0] = a.p[j] * r0;
+        Kb[j][1] = a.p[j] * r1;
+    }
+    // GU = G'' U  (5x2)
+    T GU[5][2];
+    for (int i = 0; i < 5; i++) {
+        T g0 = T(0), g1 = T(0);
+        for (int k = 0; k < 5; k++) {
+            g0 += a.G[i][k] * U[k][0];
+            g1 += a.G[i][k] * U[k][1];
+        }
+        GU[i][0] = g0;
+        GU[i][1] = g1;
+    }
+    // Sib = r r^T - U^T G'' U + U^T Kb  (then symmetrised)
+    T Sib[2][2];
+    for (int p = 0; p < 2; p++)
+        for (int q = 0; q < 2; q++) {
+            T acc = (p == 0 ? r0 : r1) * (q == 0 ? r0 : r1);
+            for (int k = 0; k < 5; k++) acc += -U[k][p] * GU[k][q] + U[k][p] * Kb[k][q];
+            Sib[p][q] = acc;
+        }
+    const T sb01 = T(0.5) * (Sib[0][1] + Sib[1][0]);
+    Sib[0][1] = sb01;
+    Sib[1][0] = sb01;
+    // Ub = -2 G'' U Si + Kb Si
+    T Ub[5][2];
+    for (int j = 0; j < 5; j++) {
+        const T m0 = -T(2) * GU[j][0] + Kb[j][0], m1 = -T(2) * GU[j][1] + Kb[j][1];
+        Ub[j][0] = m0 * i00 + m1 * i01;
+        Ub[j][1] = m0 * i01 + m1 * i11;
+    }
+    // Sb = -Si Sib Si
+    T t00 = i00 * Sib[0][0] + i01 * Sib[1][0], t01 = i00 * Sib[0][1] + i01 * Sib[1][1];
+    T t10 = i01 * Sib[0][0] + i11 * Sib[1][0], t11 = i01 * Sib[0][1] + i11 * Sib[1][1];
+    const T Sb00 = -(t00 * i00 + t01 * i01), Sb01 = -(t00 * i01 + t01 * i11);
+    const T Sb11 = -(t10 * i01 + t11 * i11);
+    // G' = G'' + sym(G_U) + Sb on the (0:2, 0:2) block
+    for (int j = 0; j < 5; j++) {
+        a.G[j][0] += T(0.5) * Ub[j][0];
+        a.G[0][j] += T(0.5) * Ub[j][0];
+        a.G[j][1] += T(0.5) * Ub[j][1];
+        a.G[1][j] += T(0.5) * Ub[j][1];
+    }
+    a.G[0][0] += Sb00;
+    a.G[0][1] += Sb01;
+    a.G[1][0] += Sb01;
+    a.G[1][1] += Sb11;
+    // p' adjoint
+    a.p[0] -= rb0;
+    a.p[1] -= rb1;
+    *ymb = rb0;
+    *zmb = rb1;
+}
+
+}  // namespace kf
+
+namespace kf {
+
+// Per-call constants of the fit.
+template <class T>
+struct Geo {
+    T kB, sig2, smax, cmin, pitch;
+    int half;               // sectors per side
+    const T *rot_c;         // cos(m * sector width), index m + half, m in [-half, half]
+    const T *rot_s;
+    const T *xr;            // row plane radii
+};
+
+// Rotation index between frames: the sector-angle difference wrapped into (-180, 180] degrees.
+KF_HD int rot_index(int k_new, int k_old, int half) {
+    int m = (k_new % half) - (k_old % half);
+    if (2 * m > half) m -= half;
+    if (2 * m <= -half) m += half;
+    return m + half;
+}
+
+// A hit as the filter sees it: sector kh, row rh, nominal (yn, zn) and the calibration offsets
+// (xl, yc, zc): x = xr[rh] + xl, y = yn + yc, z = zn + zc.
+template <class T>
+struct FHit {
+    int k, r;
+    T xl, yn, yc, zn, zc;
+};
+
+// Rotation into the frame of the hit's sector (absolute coordinates), re-referenced to the hit.
+template <class T>
+KF_HD bool step_rotate(State<T> &s, const FHit<T> &h, const Geo<T> &g) {
+    const int m = rot_index(h.k, s.frame, g.half);
+    s.x = g.xr[s.rref] + s.x;
+    s.p[0] = s.yref + s.p[0];
+    if (!rot_fwd(s, g.rot_c[m], g.rot_s[m], g.kB, g.cmin)) return false;
+    s.x = s.x - g.xr[h.r];
+    s.p[0] = s.p[0] - h.yn;
+    s.p[1] = s.p[1] + (s.zref - h.zn);
+    s.rref = h.r;
+    s.yref = h.yn;
+    s.zref = h.zn;
+    s.frame = h.k;
+    return true;
+}
+
+// One Kalman step to hit h.  Returns false if the track leaves the domain of the local
+// parametrisation (then the fit fails).
+template <class T>
+KF_HD bool step_fwd(State<T> &s, const FHit<T> &h, const Geo<T> &g, T &chi2) {
+    if (h.k != s.frame && !step_rotate(s, h, g)) return false;
+    const T dx = T(h.r - s.rref) * g.pitch + (h.xl - s.x);
+    if (!prop_fwd(s, dx, g.kB, g.smax, h.yn - s.yref, h.zn - s.zref)) return false;
+    s.x = h.xl;
+    s.rref = h.r;
+    s.yref = h.yn;
+    s.zref = h.zn;
+    chi2 += upd_fwd_joseph(s, h.yc, h.zc, g.sig2);
+    return true;
+}
+
+// Adjoint of step_fwd (for a step that succeeded): `s_in` is the state before the step, `a` the
+// adjoint after it (overwritten with the adjoint before it); adds the adjoints of the hit's
+// calibration offsets (xl, yc, zc) to *xb, *yb, *zb.
+template <class T>
+KF_HD void step_bwd(const State<T> &s_in, const FHit<T> &h, const Geo<T> &g, Adj<T> &a, T *xb, T *yb, T *zb) {
+    State<T> s1 = s_in;
+    const bool rot = h.k != s_in.frame;
+    if (rot) step_rotate(s1, h, g);
+    const T dx = T(h.r - s1.rref) * g.pitch + (h.xl - s1.x);
+    State<T> s2 = s1;
+    prop_fwd(s2, dx, g.kB, g.smax, h.yn - s1.yref, h.zn - s1.zref);
+    s2.x = h.xl;
+    s2.rref = h.r;
+    s2.yref = h.yn;
+    s2.zref = h.zn;
+    T ymb, zmb;
+    upd_bwd(s2, h.yc, h.zc, g.sig2, a, &ymb, &zmb);
+    *yb += ymb;
+    *zb += zmb;
+    const T dxb = prop_bwd(s1, dx, g.kB, g.smax, a);
+    *xb += a.x + dxb;         // xl is both the new reference offset and part of dx
+    a.x = -dxb;               // the old offset enters only through dx
+    if (rot) {                // absolute x1, y1 = rotation; s1 offsets = absolute - constants
+        const int m = rot_index(h.k, s_in.frame, g.half);
+        rot_bwd(s_in, g.rot_c[m], g.rot_s[m], g.kB, a);
+    }
+}
+
+// Seed at the last hit E from the circle through A (first), B (middle) and E, all already in E's
+// frame: signed curvature from the three points, direction at E = chord A->E plus half the
+// turning angle, tan lambda = dz / arc.  Returns false for a degenerate triple.
+template <class T>
+KF_HD bool seed3(T ax, T ay, T az, T bx, T by, T ex, T ey, T ez, T kB, T smax, T p[5]) {
+    const T abx = bx - ax, aby = by - ay, bex = ex - bx, bey = ey - by, aex = ex - ax, aey = ey - ay;
+    const T lab = k_sqrt(abx * abx + aby * aby), lbe = k_sqrt(bex * bex + bey * bey);
+    const T lae = k_sqrt(aex * aex + aey * aey);
+    if (!(lab > T(0)) || !(lbe > T(0)) || !(lae > T(0))) return false;
+    // cross product ab x be by Kahan's fused-multiply-add determinant: for a nearly straight
+    // track the two products cancel to the sagitta, which this keeps to about one ulp
+    const T w = aby * bex;
+    const T cross = k_fma(abx, bey, -w) + k_fma(-aby, bex, w);
+    const T kappa = T(2) * cross / (lab * lbe * lae);
+    const T u = T(0.5) * kappa * lae;
+    if (!(k_abs(u) < T(1))) return false;
+    // sin(atan2(aey, aex) + asin(u)) = (aey cos(asin u) + aex u) / lae
+    const T cu = k_sqrt(T(1) - u * u);
+    const T sn = (aey * cu + aex * u) / lae;
+    if (!(k_abs(sn) < smax)) return false;
+    p[0] = ey;
+    p[1] = ez;
+    p[2] = sn;
+    p[3] = (ez - az) / (lae * asinc(u));
+    p[4] = kappa / kB;
+    return true;
+}
+
+}  // namespace kf
+
+namespace kf {
+
+// Measurement update in Joseph form: P <- A P A^T + K R K^T with A = I - K H.  The measured 2x2
+// block of A is R S^-1 (= I - P_mm S^-1, computed without cancellation), the other rows are -K.
+// Algebraically equal to upd_fwd (same state, same chi2, same covariance for the optimal gain);
+// numerically it keeps the covariance positive and avoids the large-minus-large cancellation of
+// P - U S^-1 U^T when a loose prior meets the first measurements.
+template <class T>
+KF_HD T upd_fwd_joseph(State<T> &s, T ym, T zm, T s2) {
+    const T r0 = ym - s.p[0], r1 = zm - s.p[1];
+    const T S00 = s.P[0][0] + s2, S01 = s.P[0][1], S11 = s.P[1][1] + s2;
+    const T idet = T(1) / (S00 * S11 - S01 * S01);
+    const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
+    const T chi2 = r0 * r0 * i00 + T(2) * r0 * r1 * i01 + r1 * r1 * i11;
+    T K[5][2];
+    for (int j = 0; j < 5; j++) {
+        K[j][0] = s.P[j][0] * i00 + s.P[j][1] * i01;
+        K[j][1] = s.P[j][0] * i01 + s.P[j][1] * i11;
+    }
+    // A columns 0,1 (A = I - K H): rows 0,1 = R S^-1, rows 2..4 = -K
+    T A[5][2];
+    A[0][0] = s2 * i00; A[0][1] = s2 * i01;
+    A[1][0] = s2 * i01; A[1][1] = s2 * i11;
+    for (int j = 2; j < 5; j++) { A[j][0] = -K[j][0]; A[j][1] = -K[j][1]; }
+    // B = A P  (A = [A_c | e_2 e_3 e_4 columns]):  B_ij = A_i0 P_0j + A_i1 P_1j + [i>=2] P_ij
+    T B[5][5];
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) B[i][j] = A[i][0] * s.P[0][j] + A[i][1] * s.P[1][j] + (i >= 2 ? s.P[i][j] : T(0));
+    for (int j = 0; j < 5; j++) s.p[j] += K[j][0] * r0 + K[j][1] * r1;
+    // P_new = B A^T + s2 K K^T  (lower triangle, mirrored)
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            const T v = B[i][0] * A[j][0] + B[i][1] * A[j][1] + (j >= 2 ? B[i][j] : T(0)) +
+                        s2 * (K[i][0] * K[j][0] + K[i][1] * K[j][1]);
+            s.P[i][j] = v;
+            s.P[j][i] = v;
+        }
+    return chi2;
+}
+
+}  // namespace kf

@@ -218,7 +218,7 @@ def test_fit_matches_least_squares_optimum():
     ev = _events.noise_free(n_tracks=300, seed=41, single_sector=True)
     rng = np.random.default_rng(42)
     n = 0
-    c0 = np.array([100.0, 100.0, 1.0, 1.0, 100.0])
+    c0 = np.array([1.0, 1.0, 0.01, 0.01, 1.0])
     for p, idx in _outgoing_tracks(ev, min_hits=40, max_tracks=40):
         xyz = ev.true_xyz[idx].copy()
         xyz[:, 1:] += rng.normal(0, 0.01, (len(idx), 2))
