@@ -160,6 +160,29 @@ int tpc_debug_copy(tpc_ctx *ctx, int32_t what, void *dst, int64_t dst_bytes, voi
 int tpc_profile_enable(tpc_ctx *ctx, int enable);
 int tpc_profile_read(tpc_ctx *ctx, double *ms, int32_t cap, int32_t *n_calls);
 
+/* Neighbour finding for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a library convenience.  Callers recording work into a CUDA graph by stream
+ * capture (cudaMalloc cannot be captured), plug-ins whose host framework owns all GPU memory, and
+ * real-time code that may only allocate at start-up can compute the neighbour links of
+ * tpc_track_event (the same kernels; up/down as returned by tpc_debug_copy 0 and 1) without a
+ * context or a workspace.  The scratch lives in a static device array of the library, which
+ * every GPU that loads the library keeps until the process exits (about 9 MB): it limits a call
+ * to TPC_NOALLOC_MAX_CLUSTERS clusters and TPC_NOALLOC_MAX_BINS (event, sector, row) bins; larger
+ * inputs return TPC_ERR_CAPACITY with a message on stderr.  The call allocates nothing.
+ *  - geom: host struct (only n_sectors and n_rows are used); in: device clusters as for
+ *    tpc_track_event; up, down: device int32 [n_clusters] outputs (-1 = no link); status: device
+ *    int32 [1] receiving the device-side status bits (0 = ok; may be NULL).
+ *  - The first call on a device looks up the array's device address and sets a kernel attribute;
+ *    make that first call outside any stream capture.  Later calls only enqueue work on `stream`.
+ *  - All calls on a device share the array: calls that overlap on the GPU (different streams,
+ *    or graph launches running concurrently) race and corrupt each other's results.  The array
+ *    keeps the last call's contents; the call clears what must start at zero.
+ * Errors: INVALID_ARG, CAPACITY, CUDA. */
+#define TPC_NOALLOC_MAX_CLUSTERS (1 << 20)
+#define TPC_NOALLOC_MAX_BINS 16384
+int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *in, int32_t *up, int32_t *down,
+                      int32_t *status, void *stream);
+
 /* Reading constants of the integer track finding, for comparison with an independent
  * implementation: W_LINK, D_MAX, N_SEED, M_MISS, W_F0, W_F1, V_MAX, N_MIN, W_MERGE, MERGE_XMAX,
  * MERGE_BACK.  Returns the count written (at most cap). */

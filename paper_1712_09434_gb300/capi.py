@@ -22,6 +22,8 @@ TPC_ERR_CUDA = -4
 TPC_ERR_BOUNDS = -5
 TPC_ERR_NOT_RESERVED = -6
 TPC_N_TUNE = 8
+TPC_NOALLOC_MAX_CLUSTERS = 1 << 20
+TPC_NOALLOC_MAX_BINS = 16384
 STAGES = ["grid", "links", "chains", "follow", "select", "merge", "refit", "pack", "refit_grad", "reduce"]
 
 
@@ -73,6 +75,7 @@ def _load():
     lib.tpc_strerror.restype = ctypes.c_char_p
     lib.tpc_debug_copy.argtypes = [vp, i32, vp, i64, vp]
     lib.tpc_constants.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
+    lib.tpc_links_noalloc.argtypes = [ctypes.POINTER(tpc_geometry), ctypes.POINTER(tpc_clusters), vp, vp, vp, vp]
     lib.tpc_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.tpc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(i32)]
     return lib
@@ -162,6 +165,14 @@ class Tracks:
                     par=self.par[:5 * nt].view(-1, 5).cpu().numpy(), xref=self.xref[:nt].cpu().numpy(),
                     cov=self.cov[:15 * nt].view(-1, 15).cpu().numpy(), chi2=self.chi2[:nt].cpu().numpy(),
                     ndf=self.ndf[:nt].cpu().numpy())
+
+
+def tpc_links_noalloc(geometry, clusters, up, down, status=None, stream=None):
+    """Neighbour links of `clusters` into the device tensors up/down (int32 [n_clusters]) without
+    any device allocation by the library (static scratch; see include/tpc.h).  Returns the C code."""
+    cs = clusters.struct()
+    return _lib.tpc_links_noalloc(ctypes.byref(geometry), ctypes.byref(cs), _ptr(up), _ptr(down), _ptr(status),
+                                  _stream(stream))
 
 
 def default_geometry():

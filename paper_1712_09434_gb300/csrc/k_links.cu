@@ -11,6 +11,9 @@
 // shared memory with cp.async.bulk on an mbarrier (bounded wait), then every thread takes one
 // cluster c of row r and finds, among u on r+1 and d on r-1 inside the window |dY|, |dZ| <= W_LINK,
 // the pair of minimum (D, u, d), D = (Yu+Yd-2Yc)^2 + (Zu+Zd-2Zc)^2 <= D_MAX, all in integers.
+#include <cstdio>
+#include <cstring>
+
 #include "tpc_common.cuh"
 
 namespace tpc {
@@ -262,3 +265,126 @@ void launch_links(const Work &W, cudaStream_t s) {
 }
 
 }  // namespace tpc
+
+// ---- tpc_links_noalloc: grid + neighbour finding without any device allocation ---------------
+//
+// Some callers cannot allocate device memory when they run: work recorded into a CUDA graph by
+// stream capture (cudaMalloc is not a stream operation and cannot be captured), plug-ins hosted
+// by a framework whose allocator owns the whole GPU, or real-time code that may only allocate at
+// start-up.  For them this entry point runs the same grid and neighbour-finding kernels as the
+// tracking path, with their scratch (the Z-slab grid, the work-queue counter, the status word and
+// the two geometry numbers the kernels read) in one file-scope device array.  Every GPU that loads
+// the library holds that array until the process exits; all calls on a device share it.
+
+namespace tpc {
+namespace {
+
+constexpr int NOALLOC_NPAD = TPC_NOALLOC_MAX_CLUSTERS + 8 * (TPC_NOALLOC_MAX_BINS + 2) + 64;
+constexpr size_t NOALLOC_OFF_GEOM = 0;                                          // DevGeom
+constexpr size_t NOALLOC_OFF_CNT = (sizeof(DevGeom) + 255) & ~(size_t)255;      // counters[64]
+constexpr size_t NOALLOC_OFF_ZOFF = NOALLOC_OFF_CNT + 256;
+constexpr size_t NOALLOC_OFF_GYZ =
+    (NOALLOC_OFF_ZOFF + (size_t)TPC_NOALLOC_MAX_BINS * ZOFF_STRIDE * 2 + 255) & ~(size_t)255;
+constexpr size_t NOALLOC_OFF_GLOC = (NOALLOC_OFF_GYZ + (size_t)NOALLOC_NPAD * 4 + 255) & ~(size_t)255;
+constexpr size_t NOALLOC_BYTES = (NOALLOC_OFF_GLOC + (size_t)NOALLOC_NPAD * 2 + 255) & ~(size_t)255;
+
+// Writes the geometry numbers the grid and link kernels read, and clears the counters and the
+// status word (the array keeps the previous call's contents).
+__global__ void k_noalloc_setup(unsigned char *base, int n_sectors, int n_rows) {
+    if (threadIdx.x == 0) {
+        DevGeom *g = reinterpret_cast<DevGeom *>(base + NOALLOC_OFF_GEOM);
+        g->n_sectors = n_sectors;
+        g->n_rows = n_rows;
+        g->half = n_sectors / 2;
+    }
+    int32_t *cnt = reinterpret_cast<int32_t *>(base + NOALLOC_OFF_CNT);
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) cnt[i] = 0;
+}
+
+}  // namespace
+
+}  // namespace tpc
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[tpc::NOALLOC_BYTES];
+
+#include <mutex>
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_addr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+int g_noalloc_sms[NOALLOC_MAX_DEVICES];
+
+// Once per device, with that device current: the array's device address (its name in host code is
+// only a stand-in) and the shared-memory attribute of the link kernel.
+int noalloc_setup(int dev, unsigned char **base, int *sms) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            std::fprintf(stderr, "libtpc: tpc_links_noalloc set-up failed: %s\n", cudaGetErrorString(e));
+            return TPC_ERR_CUDA;
+        }
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TPC_ERR_CUDA;
+        tpc::prepare_kernels();
+        g_noalloc_sms[dev] = n;
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *base = g_noalloc_addr[dev];
+    *sms = g_noalloc_sms[dev];
+    return TPC_OK;
+}
+}  // namespace
+
+extern "C" int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *in, int32_t *up, int32_t *down,
+                                 int32_t *status, void *stream) {
+    using namespace tpc;
+    if (!geom || !in || !in->bin_off || !up || !down || in->n_events < 1 || in->n_clusters < 0 ||
+        (in->n_clusters > 0 && (!in->pad_fp || !in->time_fp)) || geom->n_sectors < 2 || geom->n_sectors % 2 ||
+        geom->n_sectors > MAX_SECTORS || geom->n_rows < 3 || geom->n_rows > MAX_ROWS)
+        return TPC_ERR_INVALID_ARG;
+    const long long nbins = (long long)in->n_events * geom->n_sectors * geom->n_rows;
+    if (in->n_clusters > TPC_NOALLOC_MAX_CLUSTERS || nbins > TPC_NOALLOC_MAX_BINS) {
+        std::fprintf(stderr,
+                     "libtpc: tpc_links_noalloc: %d clusters in %lld (event, sector, row) bins exceed the "
+                     "static scratch (at most %d clusters and %d bins)\n",
+                     in->n_clusters, nbins, TPC_NOALLOC_MAX_CLUSTERS, TPC_NOALLOC_MAX_BINS);
+        return TPC_ERR_CAPACITY;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return TPC_ERR_CUDA;
+    unsigned char *base = nullptr;
+    int sms = 0;
+    const int rc = noalloc_setup(dev, &base, &sms);
+    if (rc != TPC_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Work W;
+    std::memset(&W, 0, sizeof(W));
+    W.pad = in->pad_fp;
+    W.tim = in->time_fp;
+    W.bin_off = in->bin_off;
+    W.n_events = in->n_events;
+    W.n_clusters = in->n_clusters;
+    W.nbins = (int)nbins;
+    W.ns = geom->n_sectors;
+    W.nr = geom->n_rows;
+    W.geom = reinterpret_cast<const DevGeom *>(base + NOALLOC_OFF_GEOM);
+    W.counters = reinterpret_cast<int32_t *>(base + NOALLOC_OFF_CNT);
+    W.status = W.counters + 63;
+    W.zoff = reinterpret_cast<uint16_t *>(base + NOALLOC_OFF_ZOFF);
+    W.gyz = reinterpret_cast<int32_t *>(base + NOALLOC_OFF_GYZ);
+    W.gloc = reinterpret_cast<uint16_t *>(base + NOALLOC_OFF_GLOC);
+    W.up = up;
+    W.down = down;
+    W.sm_count = sms;
+    k_noalloc_setup<<<1, 64, 0, s>>>(base, geom->n_sectors, geom->n_rows);
+    launch_grid(W, s);
+    launch_links(W, s);
+    if (status) {
+        const cudaError_t e = cudaMemcpyAsync(status, W.status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return TPC_ERR_CUDA;
+    }
+    return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+}
