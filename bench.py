@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 from paper_1712_09434_gb300 import synth  # noqa: E402
 
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
+# kernels of one step: tracking graph (grid 1, links 1, chains 5, follow 1, select 1, merge 17,
+# refit 1) + refit_grad (pack 1, refit_grad 1, reduce 2)
+LAUNCHES_PER_STEP = 31
 WORKLOAD = "batch-64-events-logU-100-20000-tracks-20pct-noise"
 
 
@@ -209,7 +212,7 @@ def run_native(args, rank, world):
     n_tracks, n_hits = res["n_tracks"], int(res["trk_off"][-1])
 
     out = {"ms_step": ms_all, "n_clusters": n_clusters, "n_tracks": n_tracks, "n_hits": n_hits, "clocks": clk}
-    if rank != 0:
+    if rank != 0 or args.only_step:
         return out
 
     # units for the algorithmic byte counts (outside the timed region)
@@ -336,7 +339,7 @@ def finish_native(args, res, world):
                      "algorithmic_bytes": byts[dom]},
         "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"]},
-        "gpu_launches": None,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": res["clocks"],
     }
     return line
@@ -409,6 +412,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--events", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the batched step only (no plain/adjoint/e2e/CPU legs); for profiling")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -421,7 +426,11 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     res = run_native(args, rank, world)
-    if rank == 0:
+    if rank == 0 and args.only_step:
+        print(json.dumps({"metric": METRIC, "value": res["n_clusters"] * world / (res["ms_step"] * 1e-3),
+                          "unit": "clusters/s", "ms_per_step": res["ms_step"], "steps": args.steps,
+                          "note": "--only-step (profiling run)"}), flush=True)
+    elif rank == 0:
         line = finish_native(args, res, world)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(make_batch(args.events, 2000))

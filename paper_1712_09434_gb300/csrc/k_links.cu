@@ -20,7 +20,7 @@ namespace tpc {
 
 namespace {
 
-constexpr int LINK_STAGE_CAP = 4096;   // clusters of one row staged in shared memory
+constexpr int LINK_STAGE_CAP = 2048;   // clusters of one row staged in shared memory
 
 __device__ __forceinline__ int warp_incl(int v) {
     int lane = threadIdx.x & 31;
@@ -201,30 +201,64 @@ __global__ void __launch_bounds__(128) k_links(Work W) {
         for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
             const int yc = W.pad[c], zc = W.tim[c];
             const int zl = slab_of(max(zc - W_LINK, 0)), zh = slab_of(zc + W_LINK);
+            // down-row candidates inside the window, kept in registers (a window holds a few;
+            // more than DCAP falls back to rescanning the down row for every up candidate)
+            constexpr int DCAP = 8;
+            int dyv[DCAP], dzv[DCAP], dlv[DCAP];
+            int nd = 0;
+            for (int sd = zl; sd <= zh; sd++) {
+                const int hd = rv[0].zo[sd + 1];
+                for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
+                    const int32_t vd = rv[0].yz[id];
+                    const int yd = (int16_t)(vd & 0xffff);
+                    if (yd > yc + W_LINK) break;
+                    const int zd = (int)((uint32_t)vd >> 16);
+                    if (abs(zd - zc) > W_LINK) continue;
+                    if (nd < DCAP) {
+#pragma unroll
+                        for (int k = 0; k < DCAP; k++)
+                            if (k == nd) { dyv[k] = yd; dzv[k] = zd; dlv[k] = rv[0].loc[id]; }
+                    }
+                    nd++;
+                }
+            }
             unsigned long long best = ~0ull;
-            for (int su = zl; su <= zh; su++) {
-                const int hi = rv[1].zo[su + 1];
-                for (int iu = lower_y(rv[1].yz, rv[1].zo[su], hi, yc - W_LINK); iu < hi; iu++) {
-                    const int32_t vu = rv[1].yz[iu];
-                    const int yu = (int16_t)(vu & 0xffff);
-                    if (yu > yc + W_LINK) break;
-                    const int zu = (int)((uint32_t)vu >> 16);
-                    if (abs(zu - zc) > W_LINK) continue;
-                    const int lu = rv[1].loc[iu];
-                    for (int sd = zl; sd <= zh; sd++) {
-                        const int hd = rv[0].zo[sd + 1];
-                        for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
-                            const int32_t vd = rv[0].yz[id];
-                            const int yd = (int16_t)(vd & 0xffff);
-                            if (yd > yc + W_LINK) break;
-                            const int zd = (int)((uint32_t)vd >> 16);
-                            if (abs(zd - zc) > W_LINK) continue;
-                            const long long ey = yu + yd - 2 * yc, ez = zu + zd - 2 * zc;
-                            const long long D = ey * ey + ez * ez;
-                            if (D > D_MAX) continue;
-                            const unsigned long long key =
-                                ((unsigned long long)D << 32) | ((unsigned long long)lu << 16) | rv[0].loc[id];
-                            best = key < best ? key : best;
+            if (nd > 0) {
+                for (int su = zl; su <= zh; su++) {
+                    const int hi = rv[1].zo[su + 1];
+                    for (int iu = lower_y(rv[1].yz, rv[1].zo[su], hi, yc - W_LINK); iu < hi; iu++) {
+                        const int32_t vu = rv[1].yz[iu];
+                        const int yu = (int16_t)(vu & 0xffff);
+                        if (yu > yc + W_LINK) break;
+                        const int zu = (int)((uint32_t)vu >> 16);
+                        if (abs(zu - zc) > W_LINK) continue;
+                        const unsigned long long lu = (unsigned long long)rv[1].loc[iu] << 16;
+                        if (nd <= DCAP) {
+#pragma unroll
+                            for (int k = 0; k < DCAP; k++) {
+                                if (k < nd) {
+                                    const long long ey = yu + dyv[k] - 2 * yc, ez = zu + dzv[k] - 2 * zc;
+                                    const long long D = ey * ey + ez * ez;
+                                    const unsigned long long key = ((unsigned long long)D << 32) | lu | dlv[k];
+                                    if (D <= D_MAX && key < best) best = key;
+                                }
+                            }
+                        } else {
+                            for (int sd = zl; sd <= zh; sd++) {
+                                const int hd = rv[0].zo[sd + 1];
+                                for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
+                                    const int32_t vd = rv[0].yz[id];
+                                    const int yd = (int16_t)(vd & 0xffff);
+                                    if (yd > yc + W_LINK) break;
+                                    const int zd = (int)((uint32_t)vd >> 16);
+                                    if (abs(zd - zc) > W_LINK) continue;
+                                    const long long ey = yu + yd - 2 * yc, ez = zu + zd - 2 * zc;
+                                    const long long D = ey * ey + ez * ez;
+                                    if (D > D_MAX) continue;
+                                    const unsigned long long key = ((unsigned long long)D << 32) | lu | rv[0].loc[id];
+                                    best = key < best ? key : best;
+                                }
+                            }
                         }
                     }
                 }
@@ -259,7 +293,7 @@ void prepare_kernels() {
 void launch_links(const Work &W, cudaStream_t s) {
     const size_t smem = (size_t)LINK_STAGE_CAP * 12;
     const int block = W.tune.block[1] > 0 ? W.tune.block[1] : 128;
-    int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 4;
+    int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 8;
     if (grid > W.nbins) grid = W.nbins > 0 ? W.nbins : 1;
     k_links<<<grid, block, smem, s>>>(W);
 }

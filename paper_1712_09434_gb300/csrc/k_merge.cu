@@ -81,11 +81,17 @@ __global__ void k_merge_fill(Work W) {
     }
 }
 
+// One warp per outer end S: the lanes take the candidate segments T of the reachable rows of both
+// adjacent sectors 32 at a time; the warp keeps the minimum (D, T) for S and every valid pair offers
+// (D, S) to T with a 64-bit atomicMin.
 __global__ void k_merge_match(Work W) {
     const DevGeom &g = *W.geom;
     const int n = n_chains_of(W);
     const int half = W.ns / 2;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const float pitch = (float)(g.xtab[W.nr - 1] - g.xtab[0]) / (float)(W.nr - 1);
+    for (int s = gw; s < n; s += nw) {
         if (W.seg_n[s] < N_MIN) continue;
         const int4 p1 = W.outend[2 * s], p2 = W.outend[2 * s + 1];
         const int ks = p1.w;
@@ -106,14 +112,13 @@ __global__ void k_merge_match(Work W) {
             const int b0 = (ev * W.ns + kt) * W.nr;
             // rows whose plane is within MERGE_XMAX of the extrapolation start (one row of margin;
             // the exact test is below)
-            const float pitch = (float)(g.xtab[W.nr - 1] - g.xtab[0]) / (float)(W.nr - 1);
             int r_lo = (int)floorf((float)(x2 - MERGE_XMAX - g.xtab[0]) / pitch) - 1;
             int r_hi = (int)ceilf((float)(x2 + MERGE_XMAX - g.xtab[0]) / pitch) + 1;
             r_lo = max(r_lo, 0);
             r_hi = min(r_hi, W.nr - 1);
             if (r_lo > r_hi) continue;
             const int i1 = W.mrg_off[b0 + r_hi + 1];
-            for (int i = W.mrg_off[b0 + r_lo]; i < i1; i++) {
+            for (int i = W.mrg_off[b0 + r_lo] + lane; i < i1; i += 32) {
                 const int t = W.mrg_list[i];
                 const int4 e = W.inend[t];
                 const long long XT = e.x;
@@ -129,7 +134,12 @@ __global__ void k_merge_match(Work W) {
                 atomicMin(W.bestS + t, (D << 32) | (unsigned)s);
             }
         }
-        W.bestT[s] = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v < best ? v : best;
+        }
+        if (lane == 0) W.bestT[s] = best;
     }
 }
 
@@ -188,9 +198,13 @@ __global__ void k_track_count(Work W) {
     }
 }
 
+// One warp per track: the lanes read 32 row slots of a segment at a time and write its kept hits
+// in row order (ballot prefix), then move to the next segment of the merge chain.
 __global__ void k_track_write(Work W) {
     const int nt = min(W.counters[CNT_NTRACKS], W.cap_tracks);
-    for (int tid = blockIdx.x * blockDim.x + threadIdx.x; tid < nt; tid += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int tid = gw; tid < nt; tid += nw) {
         int pos = W.trk_off[tid];
         int x = W.trk_head[tid], k = 0;
         do {
@@ -198,18 +212,23 @@ __global__ void k_track_write(Work W) {
             const int rr = W.cand_rows[x];
             const int32_t *sl = W.cand_slots + (size_t)x * W.nr;
             const int sector = (W.chain_bin[x] % (W.ns * W.nr)) / W.nr;
-            for (int r = rr & 0xffff; r <= (rr >> 16); r++) {
-                const int h = sl[r];
-                if (h < 0 || W.owner[h] != key) continue;
-                if (pos < W.cap_hits) {
-                    W.trk_hits[pos] = h;
-                    W.label[h] = tid;
-                    W.trk_pack[2 * pos] = (int32_t)((uint32_t)(W.pad[h] & 0xffff) | ((uint32_t)W.tim[h] << 16));
-                    W.trk_pack[2 * pos + 1] = sector | (r << 16);
-                } else {
-                    set_status(W, ST_CAPACITY);
+            for (int r0 = rr & 0xffff; r0 <= (rr >> 16); r0 += 32) {
+                const int r = r0 + lane;
+                const int h = r <= (rr >> 16) ? sl[r] : -1;
+                const bool kept = h >= 0 && W.owner[h] == key;
+                const unsigned m = __ballot_sync(0xffffffffu, kept);
+                if (kept) {
+                    const int p = pos + __popc(m & ((1u << lane) - 1u));
+                    if (p < W.cap_hits) {
+                        W.trk_hits[p] = h;
+                        W.label[h] = tid;
+                        W.trk_pack[2 * p] = (int32_t)((uint32_t)(W.pad[h] & 0xffff) | ((uint32_t)W.tim[h] << 16));
+                        W.trk_pack[2 * p + 1] = sector | (r << 16);
+                    } else {
+                        set_status(W, ST_CAPACITY);
+                    }
                 }
-                pos++;
+                pos += __popc(m);
             }
             x = W.next[x];
             k++;
