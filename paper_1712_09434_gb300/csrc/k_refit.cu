@@ -212,7 +212,7 @@ __device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
 // S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
 template <bool GRAD>
 __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta, const float *weight, float *ck,
-                                                    float *rec) {
+                                                    float *rec, const int32_t *order) {
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
     const int ns = W.ns, np = 1 + 2 * ns;
@@ -221,7 +221,12 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
     FitGeo fg;
     load_geo(G, fg);
     const int nt = n_tracks_of(W);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    __shared__ int s_item;
+    int32_t *qh = W.counters + CNT_Q0 + 7;
+    for (int base = queue_next(qh, blockDim.x, &s_item); base < nt; base = queue_next(qh, blockDim.x, &s_item)) {
+        const int i = base + threadIdx.x;
+        if (i >= nt) continue;
+        const int t = order[i];
         const int off = W.trk_off[t];
         int n = W.trk_off[t + 1] - off;
         if (off < 0 || n < 0 || off + n > W.cap_hits) {
@@ -259,14 +264,14 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
         int cur_sec = -1, n_ent = 0;
         float ent_d[REC_SEC], ent_a[REC_SEC];
         int ent_s[REC_SEC];
-        kf::State<float> buf[CK_K];
+        float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
         for (int q0 = ((n - 1) / CK_K) * CK_K; q0 >= 0; q0 -= CK_K) {
             const int q1 = min(q0 + CK_K, n);
             kf::State<float> st;
             ck_load(ckt + (q0 / CK_K) * CK_WORDS, st);
             float dummy = 0.f;
             for (int q = q0; q < q1; q++) {
-                buf[q - q0] = st;
+                ck_store(buf + (q - q0) * CK_WORDS, st);
                 const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q));
                 kf::step_fwd(st, m.f, fg.g, dummy);
             }
@@ -274,7 +279,9 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
                 const HitRaw h = hit_raw(W, off + n - 1 - q);
                 const HitT m = transform(G, th, ns, h);
                 float xb = 0.f, yb = 0.f, zb = 0.f;
-                kf::step_bwd(buf[q - q0], m.f, fg.g, a, &xb, &yb, &zb);
+                kf::State<float> sin_;
+                ck_load(buf + (q - q0) * CK_WORDS, sin_);
+                kf::step_bwd(sin_, m.f, fg.g, a, &xb, &yb, &zb);
                 if (q == 0) {   // the seed position is this hit's (x, y, z)
                     xb += a.x;
                     yb += a.p[0];
@@ -374,6 +381,43 @@ __global__ void k_reduce_final(Work W, int np, const double *part, double *sum_c
     }
 }
 
+// Tracks in order of decreasing hit count (counting sort on min(n, LEN_BUCKETS-1)): the adjoint
+// takes them from this list, so the 32 tracks of a warp have about the same length and the longest
+// ones start first.  The order inside a bucket does not matter (every track is independent).
+constexpr int LEN_BUCKETS = 512;
+
+__global__ void k_len_hist(Work W, int32_t *hist) {
+    const int nt = n_tracks_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int n = W.trk_off[t + 1] - W.trk_off[t];
+        atomicAdd(hist + (LEN_BUCKETS - 1 - min(max(n, 0), LEN_BUCKETS - 1)), 1);
+    }
+}
+
+__global__ void k_len_scan(int32_t *hist) {   // one block of LEN_BUCKETS threads
+    __shared__ int sh[LEN_BUCKETS];
+    const int i = threadIdx.x;
+    sh[i] = hist[i];
+    __syncthreads();
+    for (int o = 1; o < LEN_BUCKETS; o <<= 1) {
+        const int v = i >= o ? sh[i - o] : 0;
+        __syncthreads();
+        sh[i] += v;
+        __syncthreads();
+    }
+    hist[i] = i > 0 ? sh[i - 1] : 0;          // exclusive offsets
+    hist[LEN_BUCKETS + i] = 0;               // fill counters
+}
+
+__global__ void k_len_scatter(Work W, int32_t *hist, int32_t *order) {
+    const int nt = n_tracks_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int n = W.trk_off[t + 1] - W.trk_off[t];
+        const int b = LEN_BUCKETS - 1 - min(max(n, 0), LEN_BUCKETS - 1);
+        order[hist[b] + atomicAdd(hist + LEN_BUCKETS + b, 1)] = t;
+    }
+}
+
 // Hit list of caller-provided tracks -> packed (Y, Z, sector, row) per hit; the bin of a cluster is
 // found by binary search in bin_off.
 __global__ void k_pack_hits(Work W) {
@@ -419,13 +463,18 @@ void launch_refit(const Work &W, const float *theta, cudaStream_t s) {
 }
 
 void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, bool grad, float *ck, float *rec,
-                           cudaStream_t s) {
+                           int32_t *order, int32_t *hist, cudaStream_t s) {
     const int block = W.tune.block[7] > 0 ? W.tune.block[7] : 128;
     const int grid = W.tune.grid[7] > 0 ? W.tune.grid[7] : W.sm_count * 8;
+    cudaMemsetAsync(hist, 0, sizeof(int32_t) * LEN_BUCKETS, s);
+    cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
+    k_len_hist<<<W.sm_count * 4, 256, 0, s>>>(W, hist);
+    k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
+    k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
     if (grad)
-        k_refit_grad<true><<<grid, block, 0, s>>>(W, theta, weight, ck, rec);
+        k_refit_grad<true><<<grid, block, 0, s>>>(W, theta, weight, ck, rec, order);
     else
-        k_refit_grad<false><<<grid, block, 0, s>>>(W, theta, weight, ck, rec);
+        k_refit_grad<false><<<grid, block, 0, s>>>(W, theta, weight, ck, rec, order);
 }
 
 void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,

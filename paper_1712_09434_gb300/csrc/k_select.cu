@@ -26,7 +26,7 @@ __device__ __forceinline__ uint32_t key_of(int n_rows, int n_hits, int local) {
 
 // One warp per candidate inside each phase: the lanes walk the candidate's row slots 32 at a time
 // (coalesced), so claims, counts and ownership of a ~100-hit candidate take a few warp steps.
-__global__ void __launch_bounds__(256) k_select(Work W) {
+__global__ void __launch_bounds__(1024) k_select(Work W) {
     __shared__ int s_item, s_undecided;
     const DevGeom &g = *W.geom;
     const int nr = g.n_rows, ns = g.n_sectors;
@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(256) k_select(Work W) {
 }  // namespace
 
 void launch_select(const Work &W, cudaStream_t s) {
-    const int block = W.tune.block[4] > 0 ? W.tune.block[4] : 256;
-    int grid = W.tune.grid[4] > 0 ? W.tune.grid[4] : W.sm_count * 8;
+    const int block = W.tune.block[4] > 0 ? W.tune.block[4] : 1024;
+    int grid = W.tune.grid[4] > 0 ? W.tune.grid[4] : W.sm_count * 2;
     const int items = W.n_events * W.ns;
     if (grid > items) grid = items > 0 ? items : 1;
     k_select<<<grid, block, 0, s>>>(W);

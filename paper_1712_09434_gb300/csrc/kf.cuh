@@ -261,36 +261,36 @@ KF_HD T prop_bwd(const State<T> &s, T dx, T kB, T smax, Adj<T> &a) {
     PropV<T> v;
     prop_vals(s, dx, kB, smax, v);
     const T sn = s.p[2], tl = s.p[3];
-    T F[5][5];
-    for (int i = 0; i < 5; i++)
-        for (int j = 0; j < 5; j++) F[i][j] = i == j ? T(1) : T(0);
-    F[0][2] = v.F02; F[0][4] = v.F04; F[1][2] = v.F12; F[1][3] = v.F13; F[1][4] = v.F14; F[2][4] = v.F24;
-    // Fb = 2 G' F P at the six state-dependent entries
+    // F = I + F02 e0e2' + F04 e0e4' + F12 e1e2' + F13 e1e3' + F14 e1e4' + F24 e2e4'; products
+    // written out over its non-zero entries.  GF = G' F:
     T GF[5][5];
-    for (int i = 0; i < 5; i++)
-        for (int j = 0; j < 5; j++) {
-            T acc = T(0);
-            for (int k = 0; k < 5; k++) acc += a.G[i][k] * F[k][j];
-            GF[i][j] = acc;
-        }
-    T Fb[5][5];
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 5; j++) {
-            T acc = T(0);
-            for (int k = 0; k < 5; k++) acc += GF[i][k] * s.P[k][j];
-            Fb[i][j] = T(2) * acc;
-        }
-    // G <- F^T G' F
-    T Gn[5][5];
-    for (int i = 0; i < 5; i++)
-        for (int j = 0; j < 5; j++) {
-            T acc = T(0);
-            for (int k = 0; k < 5; k++) acc += F[k][i] * GF[k][j];
-            Gn[i][j] = acc;
-        }
-    for (int i = 0; i < 5; i++)
-        for (int j = 0; j < 5; j++) a.G[i][j] = Gn[i][j];
-    const T F02b = Fb[0][2], F04b = Fb[0][4], F12b = Fb[1][2], F13b = Fb[1][3], F14b = Fb[1][4], F24b = Fb[2][4];
+    for (int i = 0; i < 5; i++) {
+        GF[i][0] = a.G[i][0];
+        GF[i][1] = a.G[i][1];
+        GF[i][2] = a.G[i][2] + a.G[i][0] * v.F02 + a.G[i][1] * v.F12;
+        GF[i][3] = a.G[i][3] + a.G[i][1] * v.F13;
+        GF[i][4] = a.G[i][4] + a.G[i][0] * v.F04 + a.G[i][1] * v.F14 + a.G[i][2] * v.F24;
+    }
+    // Fb = 2 G' F P at the six state-dependent entries
+    T F02b = T(0), F04b = T(0), F12b = T(0), F13b = T(0), F14b = T(0), F24b = T(0);
+    for (int k = 0; k < 5; k++) {
+        F02b += GF[0][k] * s.P[k][2];
+        F04b += GF[0][k] * s.P[k][4];
+        F12b += GF[1][k] * s.P[k][2];
+        F13b += GF[1][k] * s.P[k][3];
+        F14b += GF[1][k] * s.P[k][4];
+        F24b += GF[2][k] * s.P[k][4];
+    }
+    F02b *= T(2); F04b *= T(2); F12b *= T(2); F13b *= T(2); F14b *= T(2); F24b *= T(2);
+    // G <- F^T G' F = F^T GF
+    for (int j = 0; j < 5; j++) {
+        a.G[0][j] = GF[0][j];
+        a.G[1][j] = GF[1][j];
+        a.G[2][j] = GF[2][j] + v.F02 * GF[0][j] + v.F12 * GF[1][j];
+        a.G[3][j] = GF[3][j] + v.F13 * GF[1][j];
+        a.G[4][j] = GF[4][j] + v.F04 * GF[0][j] + v.F14 * GF[1][j] + v.F24 * GF[2][j];
+    }
+
     // state outputs: y' = y + dx T, z' = z + tl arc, s' = s2, tl' = tl, q' = q, x' = xh
     const T ypb = a.p[0], zpb = a.p[1], spb = a.p[2];
     T yb = ypb, zb = zpb, tlb = a.p[3], qb = a.p[4];

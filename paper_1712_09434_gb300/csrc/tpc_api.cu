@@ -24,6 +24,7 @@ struct tpc_ctx {
     Work ws;                  // workspace part of the kernel arguments
     float *ck, *rec;
     double *part;
+    int32_t *order, *lhist;   // tracks by decreasing length for the adjoint
     // batch graph cache
     cudaStream_t cap_stream;
     cudaGraphExec_t gexec;
@@ -110,6 +111,8 @@ size_t layout(tpc_ctx *c, char *base) {
     carve(cur, c->ck, (size_t)refit_ck_words((int)N, (int)C));
     carve(cur, c->rec, (size_t)refit_rec_words((int)C));
     carve(cur, c->part, (size_t)refit_part_doubles((int)C, c->hgeom.n_sectors));
+    carve(cur, c->order, C + 1);
+    carve(cur, c->lhist, 1024);
     w.cap_chains = c->cap_chains;
     return (size_t)(cur - base);
 }
@@ -128,6 +131,9 @@ int validate_out(const tpc_tracks *o) {
         return TPC_ERR_INVALID_ARG;
     return TPC_OK;
 }
+
+// largest block size each tunable kernel is compiled for (__launch_bounds__)
+const int kMaxBlock[TPC_N_TUNE] = {256, 128, 256, 128, 1024, 1024, 128, 128};
 
 Work make_work(const tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *o, const tpc_tuning *tune) {
     Work w = c->ws;
@@ -157,7 +163,7 @@ Work make_work(const tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *o, co
     std::memset(&w.tune, 0, sizeof(w.tune));
     if (tune) {
         for (int k = 0; k < TPC_N_TUNE; k++) {
-            w.tune.block[k] = tune->block[k] > 0 && tune->block[k] % 32 == 0 && tune->block[k] <= 512 ? tune->block[k] : 0;
+            w.tune.block[k] = tune->block[k] > 0 && tune->block[k] % 32 == 0 && tune->block[k] <= kMaxBlock[k] ? tune->block[k] : 0;
             w.tune.grid[k] = tune->ctas_per_sm[k] > 0 ? tune->ctas_per_sm[k] * c->sm_count : 0;
             w.tune.chunk[k] = tune->chunk[k] > 0 ? tune->chunk[k] : 0;
         }
@@ -359,7 +365,7 @@ int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, co
     TPC_CUDA(cudaMemcpyAsync(W.counters + CNT_NTRACKS, trk->n_tracks, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     launch_pack_hits(W, s);
     if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[1], s));
-    launch_refit_grad_fit(W, theta, weight, grad != nullptr, c->ck, c->rec, s);
+    launch_refit_grad_fit(W, theta, weight, grad != nullptr, c->ck, c->rec, c->order, c->lhist, s);
     if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[2], s));
     launch_refit_grad_reduce(W, sum_chi2, grad, c->rec, c->part, s);
     if (prof) {
