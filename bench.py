@@ -57,7 +57,9 @@ def make_batch(n_events, seed0):
     b = synth.concat_events(evs)
     d = dict(pad=b.pad_fp, tim=b.time_fp, bin_off=b.bin_off, ev_off=b.ev_off,
              ev_bin_off=np.stack([e.bin_off for e in evs]))
-    np.savez(cache, **d)
+    tmp = cache[:-4] + ".tmp%d.npz" % os.getpid()
+    np.savez(tmp, **d)
+    os.replace(tmp, cache)
     log("generated %d events, %d clusters in %.1f s" % (n_events, b.n_clusters, time.time() - t))
     return d
 
@@ -126,13 +128,33 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def shard_seed0(rank):
+    """First event seed of a rank: weak scaling, every rank tracks its own batch of events with no
+    data exchange (events are independent; the seeds of two ranks never overlap for <= 1000 events)."""
+    return 2000 + 1000 * rank
+
+
+def aggregate(ms_local, units_local, world, device="cpu"):
+    """Whole-job timing over ranks: the step time is the slowest rank's, the units are the sum over
+    ranks; value = units / time.  world == 1 needs no process group."""
+    if world <= 1:
+        return float(ms_local), int(units_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([int(units_local)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def run_native(args, rank, world):
     import torch
     from paper_1712_09434_gb300 import capi
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda")
-    seed0 = 2000 + 1000 * rank          # weak scaling: every rank tracks its own 64 events
+    seed0 = shard_seed0(rank)
     d = make_batch(args.events, seed0)
     n_clusters = int(d["pad"].shape[0])
     n_ev = args.events
@@ -201,18 +223,49 @@ def run_native(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms_all = ms_step
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_all = float(t.item())
+    ms_all, n_cl_all = aggregate(ms_step, n_clusters, world, dev)
     st = ctx.tpc_sync_status()
     assert st == 0, st
     res = tr.to_host()
     n_tracks, n_hits = res["n_tracks"], int(res["trk_off"][-1])
 
-    out = {"ms_step": ms_all, "n_clusters": n_clusters, "n_tracks": n_tracks, "n_hits": n_hits, "clocks": clk}
-    if rank != 0 or args.only_step:
+    out = {"ms_step": ms_all, "n_clusters": n_clusters, "n_clusters_all": n_cl_all, "n_tracks": n_tracks,
+           "n_hits": n_hits, "clocks": clk}
+    if args.only_step:
+        return out
+
+    # end to end through the binding with host (pinned) buffers
+    h_pad = torch.from_numpy(d["pad"]).pin_memory()
+    h_tim = torch.from_numpy(d["tim"].view(np.int16)).pin_memory()
+    h_bo = torch.from_numpy(d["bin_off"]).pin_memory()
+    h_label = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
+    h_off = torch.empty(cap_t + 1, dtype=torch.int32).pin_memory()
+    h_hits = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
+    h_par = torch.empty(cap_t * 5, dtype=torch.float32).pin_memory()
+    h_red = torch.empty(74, dtype=torch.float64).pin_memory()
+    d_pad, d_tim, d_bo = cl.pad_fp, cl.time_fp, cl.bin_off
+
+    def e2e():
+        d_pad.copy_(h_pad, non_blocking=True)
+        d_tim.copy_(h_tim, non_blocking=True)
+        d_bo.copy_(h_bo, non_blocking=True)
+        step()
+        h_label.copy_(tr.label[:n_clusters], non_blocking=True)
+        h_off.copy_(tr.trk_off[:cap_t + 1], non_blocking=True)
+        h_hits.copy_(tr.trk_hits[:n_clusters], non_blocking=True)
+        h_par.copy_(tr.par[:cap_t * 5], non_blocking=True)
+        h_red[:1].copy_(s_chi2, non_blocking=True)
+        h_red[1:].copy_(grad, non_blocking=True)
+
+    if world > 1:
+        torch.distributed.barrier()
+    ms_e2e, _ = timed(e2e, max(1, min(args.steps, 5)), 1)
+    ms_e2e, _ = aggregate(ms_e2e, n_clusters, world, dev)
+    h2d = h_pad.numel() * 2 + h_tim.numel() * 2 + h_bo.numel() * 4
+    d2h = (h_label.numel() + h_off.numel() + h_hits.numel()) * 4 + h_par.numel() * 4 + h_red.numel() * 8
+
+    out.update(ms_e2e=ms_e2e, h2d=h2d, d2h=d2h)
+    if rank != 0:
         return out
 
     # units for the algorithmic byte counts (outside the timed region)
@@ -252,35 +305,8 @@ def run_native(args, rank, world):
     th5 = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
     ms_grad, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5), 10, 3)
 
-    # end to end through the binding with host (pinned) buffers
-    h_pad = torch.from_numpy(d["pad"]).pin_memory()
-    h_tim = torch.from_numpy(d["tim"].view(np.int16)).pin_memory()
-    h_bo = torch.from_numpy(d["bin_off"]).pin_memory()
-    h_label = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
-    h_off = torch.empty(cap_t + 1, dtype=torch.int32).pin_memory()
-    h_hits = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
-    h_par = torch.empty(cap_t * 5, dtype=torch.float32).pin_memory()
-    h_red = torch.empty(74, dtype=torch.float64).pin_memory()
-    d_pad, d_tim, d_bo = cl.pad_fp, cl.time_fp, cl.bin_off
-
-    def e2e():
-        d_pad.copy_(h_pad, non_blocking=True)
-        d_tim.copy_(h_tim, non_blocking=True)
-        d_bo.copy_(h_bo, non_blocking=True)
-        step()
-        h_label.copy_(tr.label[:n_clusters], non_blocking=True)
-        h_off.copy_(tr.trk_off[:cap_t + 1], non_blocking=True)
-        h_hits.copy_(tr.trk_hits[:n_clusters], non_blocking=True)
-        h_par.copy_(tr.par[:cap_t * 5], non_blocking=True)
-        h_red[:1].copy_(s_chi2, non_blocking=True)
-        h_red[1:].copy_(grad, non_blocking=True)
-
-    ms_e2e, _ = timed(e2e, max(1, min(args.steps, 5)), 1)
-    h2d = h_pad.numel() * 2 + h_tim.numel() * 2 + h_bo.numel() * 4
-    d2h = (h_label.numel() + h_off.numel() + h_hits.numel()) * 4 + h_par.numel() * 4 + h_red.numel() * 8
-
-    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), ms_e2e=ms_e2e,
-               h2d=h2d, d2h=d2h, prof=prof, n_chains=n_chains, cand_hits=cand_hits)
+    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
+               n_chains=n_chains, cand_hits=cand_hits)
     ctx.close()
     return out
 
@@ -305,7 +331,7 @@ def stage_bytes(u):
 def finish_native(args, res, world):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    n_cl_total = res["n_clusters"] * world
+    n_cl_total = res["n_clusters_all"]
     value = n_cl_total / (res["ms_step"] * 1e-3)
     prof, n_calls = res["prof"]
     k = max(n_calls, 1)
@@ -330,7 +356,7 @@ def finish_native(args, res, world):
                    "step": "tpc_track_batch (CUDA graph) + tpc_refit_grad over the batch"},
         "plain": {"value": plain_value, "unit": "clusters/s", "ms_per_step": res["ms_plain"],
                   "form": "tpc_track_event + tpc_refit_grad per event, same 64 events"},
-        "batched_gain": value / world / plain_value,
+        "batched_gain": res["n_clusters"] / (res["ms_step"] * 1e-3) / plain_value,
         "adjoint": {"value": res["ms_grad_event"] * 1e3, "unit": "us/event",
                     "event": "central, 20000 tracks, injected calibration", "tracks": res["n_tracks_c5"]},
         "stage_ms": stage_ms,
@@ -427,7 +453,7 @@ def main():
     __graft_entry__.build()
     res = run_native(args, rank, world)
     if rank == 0 and args.only_step:
-        print(json.dumps({"metric": METRIC, "value": res["n_clusters"] * world / (res["ms_step"] * 1e-3),
+        print(json.dumps({"metric": METRIC, "value": res["n_clusters_all"] / (res["ms_step"] * 1e-3),
                           "unit": "clusters/s", "ms_per_step": res["ms_step"], "steps": args.steps,
                           "note": "--only-step (profiling run)"}), flush=True)
     elif rank == 0:

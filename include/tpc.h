@@ -183,6 +183,13 @@ int tpc_profile_read(tpc_ctx *ctx, double *ms, int32_t cap, int32_t *n_calls);
 int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *in, int32_t *up, int32_t *down,
                       int32_t *status, void *stream);
 
+/* Self-test of the failure path of a bounded device-side wait: a kernel waits on an mbarrier that
+ * nothing arrives at, gives up after spin_limit (1..2^20) polls, writes TPC_ERR_TIMEOUT to *status
+ * (device int32) and returns; the context stays usable.  The same bounded wait guards the bulk
+ * copies of the neighbour-finding kernel.  The paper has no counterpart (diagnostics).
+ * Errors: INVALID_ARG, CUDA. */
+int tpc_selftest_wait_timeout(int32_t *status, int32_t spin_limit, void *stream);
+
 /* Reading constants of the integer track finding, for comparison with an independent
  * implementation: W_LINK, D_MAX, N_SEED, M_MISS, W_F0, W_F1, V_MAX, N_MIN, W_MERGE, MERGE_XMAX,
  * MERGE_BACK.  Returns the count written (at most cap). */

@@ -2,6 +2,8 @@
 from __future__ import annotations
 
 import concurrent.futures
+import contextlib
+import fcntl
 import os
 import shutil
 import subprocess
@@ -37,11 +39,33 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
-def build(verbose=False, force=False):
+@contextlib.contextmanager
+def _locked():
+    """Serialise builds of concurrent processes (several ranks on one node start together)."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as f:
+        fcntl.flock(f, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(f, fcntl.LOCK_UN)
+
+
+def _up_to_date():
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "tpc.h")]
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)
+
+
+def build(verbose=False, force=False):
+    if not force and _up_to_date():
         return LIB
+    with _locked():
+        if force or not _up_to_date():
+            _build(verbose)
+    return LIB
+
+
+def _build(verbose):
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         res = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     if verbose:
@@ -51,7 +75,6 @@ def build(verbose=False, force=False):
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp] + [o for o, _ in res]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
-    return LIB
 
 
 if __name__ == "__main__":

@@ -76,6 +76,7 @@ def _load():
     lib.tpc_debug_copy.argtypes = [vp, i32, vp, i64, vp]
     lib.tpc_constants.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
     lib.tpc_links_noalloc.argtypes = [ctypes.POINTER(tpc_geometry), ctypes.POINTER(tpc_clusters), vp, vp, vp, vp]
+    lib.tpc_selftest_wait_timeout.argtypes = [vp, i32, vp]
     lib.tpc_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.tpc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(i32)]
     return lib

@@ -43,7 +43,10 @@ __global__ void __launch_bounds__(256) k_grid(Work W) {
         const int c0 = W.bin_off[b], c1 = W.bin_off[b + 1];
         const int cnt = c1 - c0;
         if (cnt < 0 || cnt > 65535) {
+            // row-local indices are 16 bit: flag the bin and give it an empty slab table, so that
+            // neighbour searches into it find nothing
             if (lane == 0) set_status(W, ST_BOUNDS);
+            for (int i = lane; i <= NZB; i += 32) W.zoff[(size_t)b * ZOFF_STRIDE + i] = 0;
             continue;
         }
         const int ps = pstart_of(c0, b);
@@ -107,8 +110,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = SPIN_LIMIT) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -420,5 +423,30 @@ extern "C" int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *i
         const cudaError_t e = cudaMemcpyAsync(status, W.status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return TPC_ERR_CUDA;
     }
+    return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
+}
+
+// ---- tpc_selftest_wait_timeout: the bounded-wait failure path, exercised on purpose ------------
+namespace tpc {
+namespace {
+// Waits on an mbarrier that nothing arrives at, with a small iteration limit: the wait gives up,
+// the kernel records TPC_ERR_TIMEOUT in *status and returns (no copies in flight, no TMEM held).
+__global__ void k_selftest_wait(int32_t *status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, limit);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) *status = TPC_ERR_TIMEOUT;
+        return;
+    }
+    if (threadIdx.x == 0) *status = TPC_OK;
+}
+}  // namespace
+}  // namespace tpc
+
+extern "C" int tpc_selftest_wait_timeout(int32_t *status, int32_t spin_limit, void *stream) {
+    if (!status || spin_limit < 1 || spin_limit > (1 << 20)) return TPC_ERR_INVALID_ARG;
+    tpc::k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(status, spin_limit);
     return cudaGetLastError() == cudaSuccess ? TPC_OK : TPC_ERR_CUDA;
 }

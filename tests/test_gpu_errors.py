@@ -1,0 +1,93 @@
+"""Error paths of the C ABI on a GPU: argument validation, reservation, capacity overflow, bounds,
+and a bounded device wait that runs out.  Every failure is made on the host or by a wait that
+nothing completes; no test faults, traps or hangs the GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1712_09434_gb300 import capi
+from tests import _events, _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_invalid_arguments_and_reservation():
+    ev = _events.event("c1")
+    ctx = capi.Context()                                   # nothing reserved yet
+    cl = _gpu.clusters_of(ev)
+    tr = capi.Tracks(ev.n_clusters, 1, 1000, ev.n_clusters)
+    with pytest.raises(capi.TpcError) as e:
+        ctx.tpc_track_event(cl, tr)
+    assert e.value.code == capi.TPC_ERR_NOT_RESERVED
+    ctx.reserve(ev.n_clusters // 2, 1)
+    with pytest.raises(capi.TpcError) as e:
+        ctx.tpc_track_event(cl, tr)
+    assert e.value.code == capi.TPC_ERR_NOT_RESERVED
+    ctx.reserve(ev.n_clusters, 1)                          # grows
+    bad = capi.Tracks(ev.n_clusters, 1, 1000, ev.n_clusters)
+    bad.trk_hits = None
+    with pytest.raises(capi.TpcError) as e:
+        ctx.tpc_track_event(cl, bad)
+    assert e.value.code == capi.TPC_ERR_INVALID_ARG
+    ctx.tpc_track_event(cl, tr)
+    assert ctx.tpc_sync_status() == capi.TPC_OK
+    ctx.close()
+
+
+def test_output_capacity_overflow_is_reported_not_written():
+    ev = _events.event("c1")
+    ctx = _gpu.make_context(ev.n_clusters, 1)
+    cl = _gpu.clusters_of(ev)
+    cap_t, cap_h, tail = 8, 64, 4096
+    tr = capi.Tracks(ev.n_clusters, 1, cap_t, cap_h)
+    # each bounded output is the head of a larger buffer whose tail must stay untouched
+    outer = {}
+    for name, n, dt in [("trk_off", cap_t + 1, torch.int32), ("trk_hits", cap_h, torch.int32),
+                        ("par", 5 * cap_t, torch.float32), ("cov", 15 * cap_t, torch.float32),
+                        ("chi2", cap_t, torch.float32), ("ndf", cap_t, torch.int32), ("xref", cap_t, torch.float32)]:
+        big = torch.full((n + tail,), 12345, dtype=dt, device="cuda")
+        setattr(tr, name, big[:n])
+        outer[name] = (big, n)
+    ctx.tpc_track_event(cl, tr)
+    assert ctx.tpc_sync_status() == capi.TPC_ERR_CAPACITY
+    for name, (big, n) in outer.items():
+        assert bool((big[n:] == 12345).all()), name
+    assert int(tr.n_tracks.item()) > cap_t                 # the true count is still reported
+    # the context is usable afterwards and gives the full result
+    tr2 = capi.Tracks(ev.n_clusters, 1, 4096, ev.n_clusters)
+    ctx.tpc_track_event(cl, tr2)
+    assert ctx.tpc_sync_status() == capi.TPC_OK
+    assert int(tr2.n_tracks.item()) == int(tr.n_tracks.item())
+    ctx.close()
+
+
+def test_row_bin_beyond_the_local_index_range_is_a_bounds_error():
+    # 70000 clusters in one (sector, row) bin: row-local indices are 16 bit
+    n = 70000
+    pad = np.sort(np.random.default_rng(1).integers(-1000, 1000, n)).astype(np.int16)
+    tim = np.full(n, 1000, np.uint16)
+    bin_off = np.zeros(36 * 159 + 1, np.int32)
+    bin_off[5:] = n                                          # all in bin 4 (sector 0, row 4)
+    ctx = _gpu.make_context(n, 1)
+    cl = capi.Clusters.from_numpy(pad, tim, bin_off, 1)
+    tr = capi.Tracks(n, 1, 1024, n)
+    ctx.tpc_track_event(cl, tr)
+    assert ctx.tpc_sync_status() == capi.TPC_ERR_BOUNDS
+    ctx.close()
+
+
+def test_bounded_wait_times_out_and_reports():
+    st = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+    rc = capi.lib().tpc_selftest_wait_timeout(ctypes.c_void_p(st.data_ptr()), 1000,
+                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == capi.TPC_OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == capi.TPC_ERR_TIMEOUT
+    # the context and the device stay usable
+    ev = _events.event("c1")
+    ctx = _gpu.make_context(ev.n_clusters, 1)
+    g = _gpu.run(ctx, _gpu.clusters_of(ev))
+    assert g["n_tracks"] > 50
+    ctx.close()
