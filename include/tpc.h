@@ -131,9 +131,26 @@ int tpc_track_batch(tpc_ctx *ctx, const tpc_clusters *in, tpc_tracks *out, const
  * skipped), written to *sum_chi2 (device double); if grad is not NULL, its gradient
  * d(objective)/d(theta) (device, 1 + 2*n_sectors doubles) from the adjoint of the refit.  FP32
  * Kalman arithmetic; FP64 cross-track reductions in a fixed order (deterministic).
- * Errors: INVALID_ARG, NOT_RESERVED, CUDA; device-side errors via tpc_sync_status. */
+ * anchor (device float [n_tracks][8], 16-byte aligned, or NULL): reference measurements at the
+ * production vertex that make the calibration identifiable (section 6: drift calibration against
+ * inner-tracker tracks).  Per track: [0] sigma_v of the vertex point (y, z) = (0, 0) at x = 0 in
+ * the frame of the first hit's sector; [1], [2] z0 and its sigma; [3], [4] tan lambda and sigma;
+ * [5], [6] q/pT and sigma; [7] unused.  A sigma <= 0 leaves its term out; a track with any term
+ * takes the exact helix step from its first hit to x = 0 (a failed step drops the track) and adds
+ * the chi2 of each term to chi2[t].
+ * error_model: TPC_ERRORS_FIXED takes measurement errors sigma = 0.1 cm in the calibrated y and z
+ * (the fit of the tracking); TPC_ERRORS_RAW takes them in the raw coordinates and carries them
+ * through the transformation (sigma (1 + a_k g) in y, sigma s_vd in z, g the radial factor above),
+ * which makes the objective -2 log L up to a constant for Gaussian raw errors: with fixed
+ * calibrated errors a theta that shrinks the data also shrinks the residuals, and the minimum of
+ * the sum of chi2 is biased towards it.
+ * Errors: INVALID_ARG (also a misaligned anchor or an unknown error_model), NOT_RESERVED, CUDA;
+ * device-side errors via tpc_sync_status. */
+#define TPC_ERRORS_FIXED 0
+#define TPC_ERRORS_RAW 1
 int tpc_refit_grad(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, const double *theta,
-                   const float *weight, double *sum_chi2, double *grad, void *stream);
+                   const float *weight, const float *anchor, int32_t error_model, double *sum_chi2, double *grad,
+                   void *stream);
 
 /* Wait for `stream` and return the device status word of the last calls (then clear it). */
 int tpc_sync_status(tpc_ctx *ctx, void *stream);
@@ -147,7 +164,9 @@ const char *tpc_strerror(int code);
  * 4 chain_len[C], 5 cand_n[C], 6 cand_slots[C*n_rows] (cluster per row, -1 = miss, valid inside
  * the candidate's row range), 7 cand_rows[C] (first row | last row << 16), 8 seg_n[C] (kept hits,
  * 0 if rejected), 9 next[C] (merge successor or -1), 10 counters[16] (0 chains, 1 tracks, 2 hits,
- * 3 largest number of selection rounds).  At most dst_bytes bytes are copied. */
+ * 3 largest number of selection rounds), 11 the per-track records of the last tpc_refit_grad
+ * (26 floats per track: weighted chi2, d/ds_vd, then 8 x (sector as int32 bits or -1, d/dd_k,
+ * d/da_k); a track that was not fitted has chi2 0).  At most dst_bytes bytes are copied. */
 int tpc_debug_copy(tpc_ctx *ctx, int32_t what, void *dst, int64_t dst_bytes, void *stream);
 
 /* Per-stage timing.  tpc_profile_enable(ctx, 1) makes later calls record CUDA events between their

@@ -189,32 +189,49 @@ def _weights(weight, n_trk):
     return w
 
 
-def chi2_total(pad, tim, bin_off, trk_off, trk_hits, theta, g=None, weight=None):
-    """Weighted sum of chi2 (weight per track, None = 1) of the FP64 refit at calibration theta."""
+def _refs(ref, n_trk):
+    if ref is None:
+        return None
+    r = np.ascontiguousarray(ref, np.float64).reshape(-1)
+    assert r.shape[0] == 8 * n_trk
+    return r
+
+
+def chi2_total(pad, tim, bin_off, trk_off, trk_hits, theta, g=None, weight=None, ref=None, mode=0):
+    """Weighted sum of chi2 (weight per track, None = 1) of the FP64 refit at calibration theta;
+    ref [T, 8] (None = none) adds the reference measurements at the vertex of every track; mode 1
+    takes the measurement errors in the raw coordinates, scaled into the calibrated ones by the
+    transformation (-2 log L for Gaussian raw errors)."""
     gg = g if g is not None else geometry()
     th = np.ascontiguousarray(theta, np.float64)
     nt = trk_off.shape[0] - 1
     w = _weights(weight, nt)
+    r = _refs(ref, nt)
     return lib().or_chi2_total(ctypes.byref(gg), _p(np.ascontiguousarray(pad, np.int16)),
                                _p(np.ascontiguousarray(tim, np.uint16)), _p(np.ascontiguousarray(bin_off, np.int32)),
                                ctypes.c_int32(pad.shape[0]), ctypes.c_int32(nt),
                                _p(np.ascontiguousarray(trk_off, np.int32)), _p(np.ascontiguousarray(trk_hits, np.int32)),
-                               _p(w) if w is not None else ctypes.c_void_p(0), _p(th))
+                               _p(w) if w is not None else ctypes.c_void_p(0),
+                               _p(r) if r is not None else ctypes.c_void_p(0), ctypes.c_int32(mode), _p(th))
 
 
-def grad_fd(pad, tim, bin_off, trk_off, trk_hits, theta, h=(1e-6, 1e-4, 1e-4), g=None, weight=None):
+def grad_fd(pad, tim, bin_off, trk_off, trk_hits, theta, h=(1e-6, 1e-4, 1e-4), g=None, weight=None, ref=None,
+            mode=0):
     """Reference gradient d(sum w chi2)/d(theta) by FP64 central differences."""
     gg = g if g is not None else geometry()
     th = np.ascontiguousarray(theta, np.float64)
     nt = trk_off.shape[0] - 1
     w = _weights(weight, nt)
+    r = _refs(ref, nt)
     grad = np.empty(1 + 2 * gg.n_sectors)
     hh = np.asarray(h, np.float64)
     rc = lib().or_grad_fd(ctypes.byref(gg), _p(np.ascontiguousarray(pad, np.int16)),
                           _p(np.ascontiguousarray(tim, np.uint16)), _p(np.ascontiguousarray(bin_off, np.int32)),
                           ctypes.c_int32(pad.shape[0]), ctypes.c_int32(nt),
                           _p(np.ascontiguousarray(trk_off, np.int32)), _p(np.ascontiguousarray(trk_hits, np.int32)),
-                          _p(w) if w is not None else ctypes.c_void_p(0), _p(th), _p(hh), _p(grad))
+                          _p(w) if w is not None else ctypes.c_void_p(0),
+                          _p(r) if r is not None else ctypes.c_void_p(0), ctypes.c_int32(mode), _p(th), _p(hh),
+                          _p(grad))
     assert rc == 0, rc
     return grad
 
@@ -239,8 +256,9 @@ def transform(sector, row, pad, tim, theta, g=None):
     return xyz[:n]
 
 
-def fit_xyz(sector, xyz, g=None):
-    """S8 on exact points (hit order): (ok, par[5], xref, cov[15], chi2)."""
+def fit_xyz(sector, xyz, g=None, ref=None):
+    """S8 on exact points (hit order): (ok, par[5], xref, cov[15], chi2).  With ref (8 values) the
+    reference measurements at the vertex are added and the state is reported at x = 0."""
     nh = len(sector)
     par = np.zeros(5)
     cov = np.zeros(15)
@@ -248,7 +266,8 @@ def fit_xyz(sector, xyz, g=None):
     chi2 = ctypes.c_double(0.0)
     ok = lib().or_fit_xyz(_geom(g), ctypes.c_int32(nh), _p(np.ascontiguousarray(sector, np.int32)),
                           _p(np.ascontiguousarray(xyz, np.float64)), _p(par), ctypes.byref(xref), _p(cov),
-                          ctypes.byref(chi2))
+                          ctypes.byref(chi2),
+                          _p(np.ascontiguousarray(ref, np.float64)) if ref is not None else ctypes.c_void_p(0))
     return bool(ok == 1), par, xref.value, cov, chi2.value
 
 

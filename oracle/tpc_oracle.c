@@ -450,7 +450,9 @@ done:
  * rho = |(x_r, y)|.  The fit runs from the last hit of the track to the first, with the local
  * helix state (y, z, sin phi, tan lambda, q/pT) at x in the frame of the current hit's sector.
  * ========================================================================================== */
-typedef struct { double x, y, z; } or_pt;
+/* A point under calibration theta; jy, jz = factors by which the transformation scales a raw
+ * y and z error (1 + a_k g(rho) and s_vd; the change of g across a pad row is neglected). */
+typedef struct { double x, y, z, jy, jz; } or_pt;
 
 static double sector_alpha(const or_geom *g, int k) { return ((k % (g->n_sectors / 2)) + 0.5) * 2.0 * g->half_angle; }
 
@@ -465,6 +467,8 @@ static or_pt transform(const or_geom *g, double x_first, double span, int k, int
     double sc = 1.0 + th[1 + ns + k] * (rho - x_first) / (span * rho);
     p.x = xr * sc;
     p.y = y * sc;
+    p.jy = sc;
+    p.jz = th[0];
     return p;
 }
 
@@ -557,10 +561,11 @@ static void kf_propagate(const or_geom *g, or_kf *s, double xh) {
     s->x = xh;
 }
 
-/* Measurement update with (y, z): gain K = P H^T S^-1, P <- (I - K H) P then symmetrised. */
-static void kf_update(or_kf *s, double ym, double zm) {
+/* Measurement update with (y, z) of variances (vy, vz): gain K = P H^T S^-1, P <- (I - K H) P
+ * then symmetrised. */
+static void kf_update(or_kf *s, double ym, double zm, double vy, double vz) {
     double r0 = ym - s->p[0], r1 = zm - s->p[1];
-    double S00 = s->P[0][0] + OR_SIGMA2, S01 = s->P[0][1], S11 = s->P[1][1] + OR_SIGMA2;
+    double S00 = s->P[0][0] + vy, S01 = s->P[0][1], S11 = s->P[1][1] + vz;
     double det = S00 * S11 - S01 * S01;
     double i00 = S11 / det, i01 = -S01 / det, i11 = S00 / det;
     s->chi2 += r0 * r0 * i00 + 2.0 * r0 * r1 * i01 + r1 * r1 * i11;
@@ -618,9 +623,14 @@ static const double OR_C0[5] = {1.0, 1.0, 0.01, 0.01, 1.0};
 
 /* Fit given points: measurements m[i] in the frame of sector ks[i] (hit order of the track).  The
  * seed takes sin phi, tan lambda and q/pT from the circle through the nominal points a, b, e
- * (first, middle, last hit) and its position from the last measurement.  Returns 1 on success. */
+ * (first, middle, last hit) and its position from the last measurement.  Returns 1 on success.
+ * mode 0: measurement errors sigma in y and z (the fit of section 3).  mode 1: errors sigma in
+ * the raw coordinates, carried into the calibrated ones by the transformation (sigma jy,
+ * sigma jz); chi2 is then -2 log L up to a theta-independent constant for raw errors that are
+ * Gaussian with fixed sigma, and a change of theta that only rescales the data leaves it
+ * unchanged (with fixed calibrated errors, shrinking the data would lower chi2). */
 static int fit_points(const or_geom *g, int nh, const int *ks, const or_pt *m, const or_pt *a, const or_pt *b,
-                      const or_pt *e, or_kf *s) {
+                      const or_pt *e, int mode, or_kf *s) {
     memset(s, 0, sizeof(*s));
     if (!kf_seed(g, a, ks[0], b, ks[(nh - 1) / 2], e, ks[nh - 1], s->p)) return 0;
     /* direction and curvature from the nominal circle; position at the last measurement itself */
@@ -635,15 +645,91 @@ static int fit_points(const or_geom *g, int nh, const int *ks, const or_pt *m, c
         if (!s->ok) return 0;
         kf_propagate(g, s, m[i].x);
         if (!s->ok) return 0;
-        kf_update(s, m[i].y, m[i].z);
+        if (mode == 1) {
+            double vy = OR_SIGMA2 * m[i].jy * m[i].jy, vz = OR_SIGMA2 * m[i].jz * m[i].jz;
+            kf_update(s, m[i].y, m[i].z, vy, vz);
+        } else {
+            kf_update(s, m[i].y, m[i].z, OR_SIGMA2, OR_SIGMA2);
+        }
     }
+    return 1;
+}
+
+/* General measurement update with d <= 3 components idx[] of the state, measured values m[] and
+ * independent errors sig[]: S = H P H^T + R, K = P H^T S^-1, chi2 += r^T S^-1 r, p += K r,
+ * P <- (I - K H) P, symmetrised.  S^-1 by Gauss-Jordan elimination with partial pivoting. */
+static int kf_update_h(or_kf *s, int d, const int *idx, const double *m, const double *sig) {
+    double S[3][6], r[3];
+    for (int a = 0; a < d; a++) {
+        r[a] = m[a] - s->p[idx[a]];
+        for (int b = 0; b < d; b++) {
+            S[a][b] = s->P[idx[a]][idx[b]] + (a == b ? sig[a] * sig[a] : 0.0);
+            S[a][d + b] = a == b ? 1.0 : 0.0;
+        }
+    }
+    for (int c = 0; c < d; c++) {
+        int piv = c;
+        for (int a = c + 1; a < d; a++) if (fabs(S[a][c]) > fabs(S[piv][c])) piv = a;
+        if (S[piv][c] == 0.0) return 0;
+        if (piv != c) for (int b = 0; b < 2 * d; b++) { double t = S[c][b]; S[c][b] = S[piv][b]; S[piv][b] = t; }
+        double iv = 1.0 / S[c][c];
+        for (int b = 0; b < 2 * d; b++) S[c][b] *= iv;
+        for (int a = 0; a < d; a++) {
+            if (a == c) continue;
+            double f = S[a][c];
+            for (int b = 0; b < 2 * d; b++) S[a][b] -= f * S[c][b];
+        }
+    }
+    double Si[3][3];
+    for (int a = 0; a < d; a++) for (int b = 0; b < d; b++) Si[a][b] = S[a][d + b];
+    for (int a = 0; a < d; a++) for (int b = 0; b < d; b++) s->chi2 += r[a] * Si[a][b] * r[b];
+    double K[5][3];
+    for (int i = 0; i < 5; i++) for (int b = 0; b < d; b++) {
+        double v = 0.0;
+        for (int a = 0; a < d; a++) v += s->P[i][idx[a]] * Si[a][b];
+        K[i][b] = v;
+    }
+    for (int i = 0; i < 5; i++) for (int b = 0; b < d; b++) s->p[i] += K[i][b] * r[b];
+    double A[5][5];
+    for (int i = 0; i < 5; i++) for (int j = 0; j < 5; j++) {
+        double v = s->P[i][j];
+        for (int b = 0; b < d; b++) v -= K[i][b] * s->P[idx[b]][j];
+        A[i][j] = v;
+    }
+    for (int i = 0; i < 5; i++) for (int j = 0; j < 5; j++) s->P[i][j] = 0.5 * (A[i][j] + A[j][i]);
+    return 1;
+}
+
+/* Reference measurements at the production vertex (reading of the drift calibration by matching
+ * TPC tracks to inner-tracker tracks, section 6).  ref[8] of one track: ref[0] = sigma_v of the
+ * vertex point (y, z) = (0, 0) at x = 0 in the frame of the first hit's sector; (ref[1], ref[2]) =
+ * (z0, sigma), (ref[3], ref[4]) = (tan lambda, sigma), (ref[5], ref[6]) = (q/pT, sigma) of the
+ * reference track at the vertex; a sigma <= 0 leaves its term out, ref[7] is unused.  The state
+ * at the first hit is propagated to x = 0 (exact helix step), updated with the vertex point, then
+ * with the reference track's (z0, tan lambda, q/pT).  Returns 0 if the propagation fails. */
+static int kf_anchor(const or_geom *g, or_kf *s, const double *ref) {
+    int any = ref[0] > 0.0 || ref[2] > 0.0 || ref[4] > 0.0 || ref[6] > 0.0;
+    if (!any) return 1;
+    kf_propagate(g, s, 0.0);
+    if (!s->ok) return 0;
+    if (ref[0] > 0.0) {
+        int idx[2] = {0, 1};
+        double m[2] = {0.0, 0.0}, sg[2] = {ref[0], ref[0]};
+        if (!kf_update_h(s, 2, idx, m, sg)) return 0;
+    }
+    int idx[3], d = 0;
+    double m[3], sg[3];
+    const int comp[3] = {1, 3, 4};
+    for (int c = 0; c < 3; c++)
+        if (ref[2 + 2 * c] > 0.0) { idx[d] = comp[c]; m[d] = ref[1 + 2 * c]; sg[d] = ref[2 + 2 * c]; d++; }
+    if (d > 0 && !kf_update_h(s, d, idx, m, sg)) return 0;
     return 1;
 }
 
 /* Fit one track from its raw clusters: measurements transformed with theta, seed points with the
  * nominal calibration (the seed does not depend on theta). */
 static int fit_track(const or_geom *g, double x_first, double span, const int16_t *pad, const uint16_t *tim,
-                     const int32_t *bins, const int32_t *hits, int nh, const double *theta, or_kf *s) {
+                     const int32_t *bins, const int32_t *hits, int nh, const double *theta, int mode, or_kf *s) {
     double th0[1 + 2 * 64] = {0.0};
     th0[0] = 1.0;
     int nr = g->n_rows;
@@ -659,7 +745,7 @@ static int fit_track(const or_geom *g, double x_first, double span, const int16_
     or_pt a = transform(g, x_first, span, ks[0], bins[hits[0]] % nr, pad[hits[0]], tim[hits[0]], th0);
     or_pt b = transform(g, x_first, span, ks[ib], bins[hits[ib]] % nr, pad[hits[ib]], tim[hits[ib]], th0);
     or_pt e = transform(g, x_first, span, ks[nh - 1], bins[hits[nh - 1]] % nr, pad[hits[nh - 1]], tim[hits[nh - 1]], th0);
-    return fit_points(g, nh, ks, m, &a, &b, &e, s);
+    return fit_points(g, nh, ks, m, &a, &b, &e, mode, s);
 }
 
 /* S8: fit all tracks.  par[t*5] = (y, z, sin phi, tan lambda, q/pT) at xref[t] in the frame of the
@@ -676,7 +762,7 @@ int or_fit(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const
     for (int32_t t = 0; t < n_trk; t++) {
         or_kf s;
         int nh = trk_off[t + 1] - trk_off[t];
-        int ok = nh >= 3 && fit_track(&g, gin->x_first, span, pad, tim, bins, trk_hits + trk_off[t], nh, theta, &s);
+        int ok = nh >= 3 && fit_track(&g, gin->x_first, span, pad, tim, bins, trk_hits + trk_off[t], nh, theta, 0, &s);
         for (int i = 0; i < 5; i++) par[t * 5 + i] = ok ? s.p[i] : 0.0;
         int m = 0;
         for (int i = 0; i < 5; i++) for (int j = 0; j <= i; j++) cov[t * 15 + m++] = ok ? s.P[i][j] : 0.0;
@@ -689,11 +775,14 @@ int or_fit(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const
 }
 
 /* S9 reference: weighted sum of chi2 over the tracks that fit, at calibration theta.  weight may be
- * NULL (all 1); `use` (may be NULL) restricts the sum to flagged tracks (used by the differences
- * below, which only refit the tracks a parameter can change). */
+ * NULL (all 1); ref (may be NULL) adds each track's reference measurements at the vertex (see
+ * kf_anchor; a track whose propagation to the vertex fails contributes nothing); mode selects the
+ * measurement model (see fit_points: 0 fixed errors, 1 raw errors carried through the
+ * transformation); `use` (may be NULL) restricts the sum to flagged tracks (used by the differences below,
+ * which only refit the tracks a parameter can change). */
 static double chi2_sum(const or_geom *g, double x_first, double span, const int16_t *pad, const uint16_t *tim,
                        const int32_t *bins, int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits,
-                       const double *weight, const char *use, const double *theta) {
+                       const double *weight, const double *ref, int mode, const char *use, const double *theta) {
     double sum = 0.0;
     for (int32_t t = 0; t < n_trk; t++) {
         if (use && !use[t]) continue;
@@ -701,7 +790,8 @@ static double chi2_sum(const or_geom *g, double x_first, double span, const int1
         if (w == 0.0) continue;
         or_kf s;
         int nh = trk_off[t + 1] - trk_off[t];
-        if (nh >= 3 && fit_track(g, x_first, span, pad, tim, bins, trk_hits + trk_off[t], nh, theta, &s))
+        if (nh >= 3 && fit_track(g, x_first, span, pad, tim, bins, trk_hits + trk_off[t], nh, theta, mode, &s) &&
+            (!ref || kf_anchor(g, &s, ref + 8 * (size_t)t)))
             sum += w * s.chi2;
     }
     return sum;
@@ -709,12 +799,12 @@ static double chi2_sum(const or_geom *g, double x_first, double span, const int1
 
 double or_chi2_total(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
                      int32_t n, int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits, const double *weight,
-                     const double *theta) {
+                     const double *ref, int32_t mode, const double *theta) {
     or_geom g;
     if (make_geom(gin, &g)) return -1.0;
     int32_t *bins = cluster_bins(bin_off, g.n_sectors * g.n_rows, n);
     double v = chi2_sum(&g, gin->x_first, gin->x_last - gin->x_first, pad, tim, bins, n_trk, trk_off, trk_hits,
-                        weight, NULL, theta);
+                        weight, ref, mode, NULL, theta);
     free(bins);
     return v;
 }
@@ -724,7 +814,7 @@ double or_chi2_total(const or_geom_in *gin, const int16_t *pad, const uint16_t *
  * the perturbed sector are refitted for d_k and a_k (the others do not depend on them). */
 int or_grad_fd(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off, int32_t n,
                int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits, const double *weight,
-               const double *theta, const double *h, double *grad) {
+               const double *ref, int32_t mode, const double *theta, const double *h, double *grad) {
     or_geom g;
     if (make_geom(gin, &g)) return -1;
     int ns = g.n_sectors, np = 1 + 2 * ns;
@@ -743,9 +833,9 @@ int or_grad_fd(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, c
         }
         memcpy(th, theta, sizeof(double) * np);
         th[j] = theta[j] + hj;
-        double fp = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, weight, use, th);
+        double fp = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, weight, ref, mode, use, th);
         th[j] = theta[j] - hj;
-        double fm = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, weight, use, th);
+        double fm = chi2_sum(&g, gin->x_first, span, pad, tim, bins, n_trk, trk_off, trk_hits, weight, ref, mode, use, th);
         grad[j] = (fp - fm) / (2.0 * hj);
     }
     free(th); free(use); free(bins);
@@ -775,17 +865,26 @@ int or_transform(const or_geom_in *gin, int32_t n, const int32_t *sector, const 
     return 0;
 }
 
-/* S8 on exact points: hits (sector, x, y, z) in hit order, used as both measurements and seed. */
+/* S8 on exact points: hits (sector, x, y, z) in hit order, used as both measurements and seed.
+ * With ref (8 values, may be NULL) the reference measurements at the vertex are added (kf_anchor)
+ * and the state is reported at x = 0. */
 int or_fit_xyz(const or_geom_in *gin, int32_t nh, const int32_t *sector, const double *xyz, double *par,
-               double *xref, double *cov, double *chi2) {
+               double *xref, double *cov, double *chi2, const double *ref) {
     or_geom g;
     if (make_geom(gin, &g)) return -1;
     if (nh < 3 || nh > OR_MAX_ROWS * 4) return 0;
     int ks[OR_MAX_ROWS * 4];
     or_pt m[OR_MAX_ROWS * 4];
-    for (int i = 0; i < nh; i++) { ks[i] = sector[i]; m[i].x = xyz[3 * i]; m[i].y = xyz[3 * i + 1]; m[i].z = xyz[3 * i + 2]; }
+    for (int i = 0; i < nh; i++) {
+        ks[i] = sector[i];
+        m[i].x = xyz[3 * i];
+        m[i].y = xyz[3 * i + 1];
+        m[i].z = xyz[3 * i + 2];
+        m[i].jy = m[i].jz = 1.0;
+    }
     or_kf s;
-    int ok = fit_points(&g, nh, ks, m, &m[0], &m[(nh - 1) / 2], &m[nh - 1], &s);
+    int ok = fit_points(&g, nh, ks, m, &m[0], &m[(nh - 1) / 2], &m[nh - 1], 0, &s);
+    if (ok && ref) ok = kf_anchor(&g, &s, ref);
     if (!ok) return 0;
     for (int i = 0; i < 5; i++) par[i] = s.p[i];
     int k = 0;

@@ -22,6 +22,8 @@ TPC_ERR_CUDA = -4
 TPC_ERR_BOUNDS = -5
 TPC_ERR_NOT_RESERVED = -6
 TPC_N_TUNE = 8
+TPC_ERRORS_FIXED = 0
+TPC_ERRORS_RAW = 1
 TPC_NOALLOC_MAX_CLUSTERS = 1 << 20
 TPC_NOALLOC_MAX_BINS = 16384
 STAGES = ["grid", "links", "chains", "follow", "select", "merge", "refit", "pack", "refit_grad", "reduce"]
@@ -69,7 +71,8 @@ def _load():
     lib.tpc_track_event.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp]
     lib.tpc_track_batch.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks),
                                     ctypes.POINTER(tpc_tuning), vp]
-    lib.tpc_refit_grad.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp, vp, vp]
+    lib.tpc_refit_grad.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp, i32,
+                                   vp, vp, vp]
     lib.tpc_sync_status.argtypes = [vp, vp]
     lib.tpc_strerror.argtypes = [ctypes.c_int]
     lib.tpc_strerror.restype = ctypes.c_char_p
@@ -218,10 +221,14 @@ class Context:
         check(_lib.tpc_track_batch(self.handle, ctypes.byref(cs), ctypes.byref(ts), tp, _stream(stream)),
               "tpc_track_batch")
 
-    def tpc_refit_grad(self, clusters, tracks, theta, sum_chi2, grad=None, weight=None, stream=None):
+    def tpc_refit_grad(self, clusters, tracks, theta, sum_chi2, grad=None, weight=None, anchor=None,
+                       error_model=TPC_ERRORS_FIXED, stream=None):
+        """anchor: device float32 [n_tracks, 8] reference measurements at the vertex, or None;
+        error_model: TPC_ERRORS_FIXED or TPC_ERRORS_RAW (see include/tpc.h)."""
         cs, ts = clusters.struct(), tracks.struct()
         check(_lib.tpc_refit_grad(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(theta), _ptr(weight),
-                                  _ptr(sum_chi2), _ptr(grad), _stream(stream)), "tpc_refit_grad")
+                                  _ptr(anchor), int(error_model), _ptr(sum_chi2), _ptr(grad), _stream(stream)),
+              "tpc_refit_grad")
 
     def tpc_sync_status(self, stream=None):
         return _lib.tpc_sync_status(self.handle, _stream(stream))
@@ -248,19 +255,21 @@ class Context:
 
 class CalibRefit(torch.autograd.Function):
     """sum_t w_t chi2_t of the Kalman refit as a differentiable function of the calibration theta
-    (float64, [1 + 2*n_sectors]); weight (float32 [n_tracks] or None) selects the tracks.  The
-    forward call computes the adjoint gradient as well; backward scales it."""
+    (float64, [1 + 2*n_sectors]); weight (float32 [n_tracks] or None) selects the tracks, anchor
+    (float32 [n_tracks, 8] or None) adds the reference measurements at the vertex, error_model
+    picks fixed or raw measurement errors.  The forward
+    call computes the adjoint gradient as well; backward scales it."""
 
     @staticmethod
-    def forward(ctx_, theta, context, clusters, tracks, weight=None):
+    def forward(ctx_, theta, context, clusters, tracks, weight=None, anchor=None, error_model=TPC_ERRORS_FIXED):
         theta = theta.detach().to(dtype=torch.float64).contiguous()
         out = torch.empty(1, dtype=torch.float64, device=theta.device)
         grad = torch.empty_like(theta)
-        context.tpc_refit_grad(clusters, tracks, theta, out, grad, weight)
+        context.tpc_refit_grad(clusters, tracks, theta, out, grad, weight, anchor, error_model)
         ctx_.save_for_backward(grad)
         return out[0]
 
     @staticmethod
     def backward(ctx_, g):
         (grad,) = ctx_.saved_tensors
-        return g * grad, None, None, None, None
+        return g * grad, None, None, None, None, None, None

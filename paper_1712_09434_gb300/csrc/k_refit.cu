@@ -65,16 +65,23 @@ __device__ __forceinline__ HitRaw hit_raw(const Work &W, int i) {
     return h;
 }
 
-// S0: hit under theta (th[0] = s_vd, th[1+k] = d_k, th[1+ns+k] = a_k) as the filter sees it:
+// S0: hit under theta (th[0] = 1 - s_vd, th[1+k] = d_k, th[1+ns+k] = a_k) as the filter sees it.
+// The kernels take 1 - s_vd from the double theta before rounding to float, so that the drift
+// scale keeps its full precision (s_vd itself rounds to 6e-8, a shift that the vertex references
+// would notice):
 // nominal coordinates (yn = Y*lsb, zn = side*(z_max - D), exact in FP32) plus the calibration
 // offsets xl = x_r*a_k*g', yc = y_raw*a_k*g', zc = side*(1 - s_vd)*D + d_k, with the derivative
 // factors dzc/ds_vd = -side*D and g' = (rho - x_first)/(span*rho).
+// Measurement variances: with model 0 fixed (sigma^2 in y and z); with model 1 the raw errors are
+// carried through the transformation, vy = sigma^2 jy^2, vz = sigma^2 jz^2 with jy = 1 + a_k g'
+// and jz = s_vd (the change of g' across a pad row is neglected).
 struct HitT {
     kf::FHit<float> f;
-    float dzds, gp, xr, yraw;
+    float dzds, gp, xr, yraw, jy, jz;
 };
 
-__device__ __forceinline__ HitT transform(const DevGeom &G, const float *th, int ns, const HitRaw &h) {
+__device__ __forceinline__ HitT transform(const DevGeom &G, const float *th, int ns, const HitRaw &h,
+                                          int model = 0) {
     HitT o;
     const float side = h.k < G.half ? 1.f : -1.f;
     o.xr = G.xr[h.r];
@@ -84,13 +91,17 @@ __device__ __forceinline__ HitT transform(const DevGeom &G, const float *th, int
     o.f.r = h.r;
     o.f.yn = o.yraw;
     o.f.zn = side * (G.z_max - D);
-    o.f.zc = side * ((1.f - th[0]) * D) + th[1 + h.k];
+    o.f.zc = side * (th[0] * D) + th[1 + h.k];
     o.dzds = -side * D;
     const float rho = sqrtf(o.xr * o.xr + o.yraw * o.yraw);
     o.gp = (rho - G.x_first) * G.inv_span / rho;
     const float corr = th[1 + ns + h.k] * o.gp;
     o.f.xl = o.xr * corr;
     o.f.yc = o.yraw * corr;
+    o.jy = 1.f + corr;
+    o.jz = 1.f - th[0];
+    o.f.vy = model == 1 ? SIGMA2 * o.jy * o.jy : SIGMA2;
+    o.f.vz = model == 1 ? SIGMA2 * o.jz * o.jz : SIGMA2;
     return o;
 }
 
@@ -146,7 +157,7 @@ __global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
     const int ns = W.ns, np = 1 + 2 * ns;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) th[i] = theta[i];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) th[i] = i == 0 ? 1.f - theta[0] : theta[i];
     __syncthreads();
     FitGeo fg;
     load_geo(G, fg);
@@ -182,6 +193,87 @@ __global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
     }
 }
 
+// Reference measurements at the vertex of one track (reading of the drift calibration by matching
+// TPC tracks to inner-tracker tracks, section 6).  anchor[8t..8t+7] = sigma_v of the vertex point
+// (y, z) = (0, 0) at x = 0 in the frame of the first hit's sector, then (z0, sigma), (tan lambda,
+// sigma), (q/pT, sigma) of the reference track; a sigma <= 0 leaves its term out.  After the last
+// hit the state takes the exact helix step to x = 0 (stage 0) and is updated with each term
+// (stages 1-4); a failed step fails the track.
+struct Anchor {
+    float sv, z0, sz, tl, st, q, sq;
+    __device__ __forceinline__ bool any() const { return sv > 0.f || sz > 0.f || st > 0.f || sq > 0.f; }
+    __device__ __forceinline__ bool fixes_z() const { return sv > 0.f || sz > 0.f; }
+};
+constexpr int N_ANCHOR_STAGES = 5;
+
+__device__ __forceinline__ Anchor load_anchor(const float *anchor, int t) {
+    const float4 a = reinterpret_cast<const float4 *>(anchor)[2 * t];
+    const float4 b = reinterpret_cast<const float4 *>(anchor)[2 * t + 1];
+    Anchor A;
+    A.sv = a.x;
+    A.z0 = a.y;
+    A.sz = a.z;
+    A.tl = a.w;
+    A.st = b.x;
+    A.q = b.y;
+    A.sq = b.z;
+    return A;
+}
+
+__device__ __forceinline__ bool anchor_fwd(kf::State<float> &s, int j, const Anchor &A, const kf::Geo<float> &g,
+                                           float &chi2) {
+    switch (j) {
+        case 0: {
+            const float dx = -(g.xr[s.rref] + s.x);
+            if (!kf::prop_fwd(s, dx, g.kB, g.smax, -s.yref, -s.zref)) return false;
+            s.x = -g.xr[s.rref];   // absolute x = 0
+            s.yref = 0.f;
+            s.zref = 0.f;
+            return true;
+        }
+        case 1:
+            if (A.sv > 0.f) chi2 += kf::upd_fwd_joseph(s, 0.f, 0.f, A.sv * A.sv, A.sv * A.sv);
+            return true;
+        case 2:
+            if (A.sz > 0.f) chi2 += kf::upd1_fwd(s, 1, A.z0, A.sz * A.sz);
+            return true;
+        case 3:
+            if (A.st > 0.f) chi2 += kf::upd1_fwd(s, 3, A.tl, A.st * A.st);
+            return true;
+        default:
+            if (A.sq > 0.f) chi2 += kf::upd1_fwd(s, 4, A.q, A.sq * A.sq);
+            return true;
+    }
+}
+
+// Adjoint of anchor_fwd stage j; `s` is the state before the stage.
+__device__ __forceinline__ void anchor_bwd(const kf::State<float> &s, int j, const Anchor &A,
+                                           const kf::Geo<float> &g, kf::Adj<float> &a) {
+    switch (j) {
+        case 0: {
+            const float dx = -(g.xr[s.rref] + s.x);
+            const float dxb = kf::prop_bwd(s, dx, g.kB, g.smax, a);
+            a.x = -dxb;            // the state's x enters through dx only; the new x is a constant
+            return;
+        }
+        case 1:
+            if (A.sv > 0.f) {
+                float ymb, zmb, vyb, vzb;
+                kf::upd_bwd(s, 0.f, 0.f, A.sv * A.sv, A.sv * A.sv, a, &ymb, &zmb, &vyb, &vzb);
+            }
+            return;
+        case 2:
+            if (A.sz > 0.f) kf::upd1_bwd(s, 1, A.z0, A.sz * A.sz, a);
+            return;
+        case 3:
+            if (A.st > 0.f) kf::upd1_bwd(s, 3, A.tl, A.st * A.st, a);
+            return;
+        default:
+            if (A.sq > 0.f) kf::upd1_bwd(s, 4, A.q, A.sq * A.sq, a);
+            return;
+    }
+}
+
 __device__ __forceinline__ void ck_store(float *dst, const kf::State<float> &s) {
     dst[0] = s.x;
     for (int i = 0; i < 5; i++) dst[1 + i] = s.p[i];
@@ -211,12 +303,13 @@ __device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
 
 // S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
 template <bool GRAD>
-__global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta, const float *weight, float *ck,
-                                                    float *rec, const int32_t *order) {
+__global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta, const float *weight,
+                                                    const float *anchor, int model, float *ck, float *rec,
+                                                    const int32_t *order) {
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
     const int ns = W.ns, np = 1 + 2 * ns;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) th[i] = (float)theta[i];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) th[i] = (float)(i == 0 ? 1.0 - theta[0] : theta[i]);
     __syncthreads();
     FitGeo fg;
     load_geo(G, fg);
@@ -246,8 +339,15 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
         bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
         for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q
             if (GRAD && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
-            const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q));
+            const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q), model);
             ok = kf::step_fwd(s, m.f, fg.g, chi2);
+        }
+        float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
+        Anchor A{};
+        const bool use_anchor = anchor != nullptr && ok && (A = load_anchor(anchor, t)).any();
+        for (int j = 0; use_anchor && ok && j < N_ANCHOR_STAGES; j++) {
+            if (GRAD) ck_store(buf + j * CK_WORDS, s);
+            ok = anchor_fwd(s, j, A, fg.g, chi2);
         }
         r[0] = ok ? w * chi2 : 0.f;
         r[1] = 0.f;
@@ -264,7 +364,13 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
         int cur_sec = -1, n_ent = 0;
         float ent_d[REC_SEC], ent_a[REC_SEC];
         int ent_s[REC_SEC];
-        float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
+        if (use_anchor) {               // the vertex stages first, from the states kept in buf
+            for (int j = N_ANCHOR_STAGES - 1; j >= 0; j--) {
+                kf::State<float> st;
+                ck_load(buf + j * CK_WORDS, st);
+                anchor_bwd(st, j, A, fg.g, a);
+            }
+        }
         for (int q0 = ((n - 1) / CK_K) * CK_K; q0 >= 0; q0 -= CK_K) {
             const int q1 = min(q0 + CK_K, n);
             kf::State<float> st;
@@ -272,16 +378,16 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
             float dummy = 0.f;
             for (int q = q0; q < q1; q++) {
                 ck_store(buf + (q - q0) * CK_WORDS, st);
-                const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q));
+                const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q), model);
                 kf::step_fwd(st, m.f, fg.g, dummy);
             }
             for (int q = q1 - 1; q >= q0; q--) {
                 const HitRaw h = hit_raw(W, off + n - 1 - q);
-                const HitT m = transform(G, th, ns, h);
-                float xb = 0.f, yb = 0.f, zb = 0.f;
+                const HitT m = transform(G, th, ns, h, model);
+                float xb = 0.f, yb = 0.f, zb = 0.f, vyb = 0.f, vzb = 0.f;
                 kf::State<float> sin_;
                 ck_load(buf + (q - q0) * CK_WORDS, sin_);
-                kf::step_bwd(sin_, m.f, fg.g, a, &xb, &yb, &zb);
+                kf::step_bwd(sin_, m.f, fg.g, a, &xb, &yb, &zb, &vyb, &vzb);
                 if (q == 0) {   // the seed position is this hit's (x, y, z)
                     xb += a.x;
                     yb += a.p[0];
@@ -303,9 +409,10 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
                     gd = Kahan();
                     ga = Kahan();
                 }
-                gs.add(zb * m.dzds);
+                // model 1: vz = sigma^2 s_vd^2, vy = sigma^2 (1 + a_k g')^2
+                gs.add(zb * m.dzds + (model == 1 ? vzb * (2.f * SIGMA2) * m.jz : 0.f));
                 gd.add(zb);
-                ga.add((xb * m.xr + yb * m.yraw) * m.gp);
+                ga.add((xb * m.xr + yb * m.yraw + (model == 1 ? vyb * (2.f * SIGMA2) * m.jy : 0.f)) * m.gp);
             }
         }
         if (cur_sec >= 0) {
@@ -318,17 +425,18 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
             }
             n_ent++;
         }
-        // A common shift of every z of the track (hits and seed) leaves its chi2 unchanged, so the
-        // exact d/dd_k contributions of one track sum to zero.  Project the FP32 sums onto that
-        // constraint (equal share of the rounding residual to every entry): a single-sector track
-        // contributes exactly zero.
+        // Without a z reference at the vertex, a common shift of every z of the track (hits and
+        // seed) leaves its chi2 unchanged, so the exact d/dd_k contributions of one track sum to
+        // zero.  Project the FP32 sums onto that constraint (equal share of the rounding residual
+        // to every entry): a single-sector track contributes exactly zero.
         const int ne = n_ent < REC_SEC ? n_ent : REC_SEC;
+        const bool zfree = !(use_anchor && A.fixes_z());
         Kahan tot;
         for (int k = 0; k < ne; k++) tot.add(ent_d[k]);
-        const float share = ne > 0 ? tot.value() / (float)ne : 0.f;
+        const float share = ne > 0 && zfree ? tot.value() / (float)ne : 0.f;
         for (int k = 0; k < ne; k++) {
             r[2 + 3 * k] = __int_as_float(ent_s[k]);
-            r[3 + 3 * k] = w * (ne == 1 ? 0.f : ent_d[k] - share);
+            r[3 + 3 * k] = w * (ne == 1 && zfree ? 0.f : ent_d[k] - share);
             r[4 + 3 * k] = w * ent_a[k];
         }
         r[1] = w * gs.value();
@@ -462,8 +570,8 @@ void launch_refit(const Work &W, const float *theta, cudaStream_t s) {
     k_refit<<<grid, block, 0, s>>>(W, theta);
 }
 
-void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, bool grad, float *ck, float *rec,
-                           int32_t *order, int32_t *hist, cudaStream_t s) {
+void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
+                           bool grad, float *ck, float *rec, int32_t *order, int32_t *hist, cudaStream_t s) {
     const int block = W.tune.block[7] > 0 ? W.tune.block[7] : 128;
     const int grid = W.tune.grid[7] > 0 ? W.tune.grid[7] : W.sm_count * 8;
     cudaMemsetAsync(hist, 0, sizeof(int32_t) * LEN_BUCKETS, s);
@@ -472,9 +580,9 @@ void launch_refit_grad_fit(const Work &W, const double *theta, const float *weig
     k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
     k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
     if (grad)
-        k_refit_grad<true><<<grid, block, 0, s>>>(W, theta, weight, ck, rec, order);
+        k_refit_grad<true><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
     else
-        k_refit_grad<false><<<grid, block, 0, s>>>(W, theta, weight, ck, rec, order);
+        k_refit_grad<false><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
 }
 
 void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,

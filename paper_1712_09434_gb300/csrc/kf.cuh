@@ -8,7 +8,7 @@
 //   exact helix propagation to the hit's x (C = kB q/pT; sin phi2 = sin phi + C dx;
 //     dy = dx T, T = (sin phi + sin phi2)/(cos phi + cos phi2); L = dx sqrt(1+T^2);
 //     dz = tan lambda * L * asin(C L/2)/(C L/2)), covariance F P F^T with the step Jacobian,
-//   measurement update with (y, z), R = diag(s2, s2), symmetric form P - U S^-1 U^T.
+//   measurement update with (y, z), R = diag(vy, vz), symmetric form P - U S^-1 U^T.
 //
 // The adjoint propagates d(sum chi2)/d(.) backwards through one step.  Matrix adjoints use the
 // symmetric-gradient convention: for a symmetric argument P, Pb is symmetric and
@@ -373,9 +373,9 @@ KF_HD T prop_bwd(const State<T> &s, T dx, T kB, T smax, Adj<T> &a) {
 
 // ---- measurement update ----------------------------------------------------------------------
 template <class T>
-KF_HD T upd_fwd(State<T> &s, T ym, T zm, T s2) {
+KF_HD T upd_fwd(State<T> &s, T ym, T zm, T vy, T vz) {
     const T r0 = ym - s.p[0], r1 = zm - s.p[1];
-    const T S00 = s.P[0][0] + s2, S01 = s.P[0][1], S11 = s.P[1][1] + s2;
+    const T S00 = s.P[0][0] + vy, S01 = s.P[0][1], S11 = s.P[1][1] + vz;
     const T idet = T(1) / (S00 * S11 - S01 * S01);
     const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
     const T chi2 = r0 * r0 * i00 + T(2) * r0 * r1 * i01 + r1 * r1 * i11;
@@ -397,11 +397,11 @@ KF_HD T upd_fwd(State<T> &s, T ym, T zm, T s2) {
 }
 
 // Adjoint of upd_fwd with d(chi2) = 1; `s` is the state before the update.  Writes the adjoint
-// of the measurement to (*ymb, *zmb).
+// of the measurement to (*ymb, *zmb) and that of the variances (vy, vz) to (*vyb, *vzb).
 template <class T>
-KF_HD void upd_bwd(const State<T> &s, T ym, T zm, T s2, Adj<T> &a, T *ymb, T *zmb) {
+KF_HD void upd_bwd(const State<T> &s, T ym, T zm, T vy, T vz, Adj<T> &a, T *ymb, T *zmb, T *vyb, T *vzb) {
     const T r0 = ym - s.p[0], r1 = zm - s.p[1];
-    const T S00 = s.P[0][0] + s2, S01 = s.P[0][1], S11 = s.P[1][1] + s2;
+    const T S00 = s.P[0][0] + vy, S01 = s.P[0][1], S11 = s.P[1][1] + vz;
     const T idet = T(1) / (S00 * S11 - S01 * S01);
     const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
     T U[5][2], K[5][2];
@@ -473,6 +473,8 @@ KF_HD void upd_bwd(const State<T> &s, T ym, T zm, T s2, Adj<T> &a, T *ymb, T *zm
     a.p[1] -= rb1;
     *ymb = rb0;
     *zmb = rb1;
+    *vyb = Sb00;              // S = P_mm + R
+    *vzb = Sb11;
 }
 
 }  // namespace kf
@@ -498,11 +500,11 @@ KF_HD int rot_index(int k_new, int k_old, int half) {
 }
 
 // A hit as the filter sees it: sector kh, row rh, nominal (yn, zn) and the calibration offsets
-// (xl, yc, zc): x = xr[rh] + xl, y = yn + yc, z = zn + zc.
+// (xl, yc, zc): x = xr[rh] + xl, y = yn + yc, z = zn + zc; measurement variances (vy, vz).
 template <class T>
 struct FHit {
     int k, r;
-    T xl, yn, yc, zn, zc;
+    T xl, yn, yc, zn, zc, vy, vz;
 };
 
 // Rotation into the frame of the hit's sector (absolute coordinates), re-referenced to the hit.
@@ -533,15 +535,16 @@ KF_HD bool step_fwd(State<T> &s, const FHit<T> &h, const Geo<T> &g, T &chi2) {
     s.rref = h.r;
     s.yref = h.yn;
     s.zref = h.zn;
-    chi2 += upd_fwd_joseph(s, h.yc, h.zc, g.sig2);
+    chi2 += upd_fwd_joseph(s, h.yc, h.zc, h.vy, h.vz);
     return true;
 }
 
 // Adjoint of step_fwd (for a step that succeeded): `s_in` is the state before the step, `a` the
 // adjoint after it (overwritten with the adjoint before it); adds the adjoints of the hit's
-// calibration offsets (xl, yc, zc) to *xb, *yb, *zb.
+// calibration offsets (xl, yc, zc) to *xb, *yb, *zb and those of its variances to *vyb, *vzb.
 template <class T>
-KF_HD void step_bwd(const State<T> &s_in, const FHit<T> &h, const Geo<T> &g, Adj<T> &a, T *xb, T *yb, T *zb) {
+KF_HD void step_bwd(const State<T> &s_in, const FHit<T> &h, const Geo<T> &g, Adj<T> &a, T *xb, T *yb, T *zb,
+                    T *vyb, T *vzb) {
     State<T> s1 = s_in;
     const bool rot = h.k != s_in.frame;
     if (rot) step_rotate(s1, h, g);
@@ -552,10 +555,12 @@ KF_HD void step_bwd(const State<T> &s_in, const FHit<T> &h, const Geo<T> &g, Adj
     s2.rref = h.r;
     s2.yref = h.yn;
     s2.zref = h.zn;
-    T ymb, zmb;
-    upd_bwd(s2, h.yc, h.zc, g.sig2, a, &ymb, &zmb);
+    T ymb, zmb, vyb_, vzb_;
+    upd_bwd(s2, h.yc, h.zc, h.vy, h.vz, a, &ymb, &zmb, &vyb_, &vzb_);
     *yb += ymb;
     *zb += zmb;
+    *vyb += vyb_;
+    *vzb += vzb_;
     const T dxb = prop_bwd(s1, dx, g.kB, g.smax, a);
     *xb += a.x + dxb;         // xl is both the new reference offset and part of dx
     a.x = -dxb;               // the old offset enters only through dx
@@ -603,9 +608,9 @@ namespace kf {
 // numerically it keeps the covariance positive and avoids the large-minus-large cancellation of
 // P - U S^-1 U^T when a loose prior meets the first measurements.
 template <class T>
-KF_HD T upd_fwd_joseph(State<T> &s, T ym, T zm, T s2) {
+KF_HD T upd_fwd_joseph(State<T> &s, T ym, T zm, T vy, T vz) {
     const T r0 = ym - s.p[0], r1 = zm - s.p[1];
-    const T S00 = s.P[0][0] + s2, S01 = s.P[0][1], S11 = s.P[1][1] + s2;
+    const T S00 = s.P[0][0] + vy, S01 = s.P[0][1], S11 = s.P[1][1] + vz;
     const T idet = T(1) / (S00 * S11 - S01 * S01);
     const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
     const T chi2 = r0 * r0 * i00 + T(2) * r0 * r1 * i01 + r1 * r1 * i11;
@@ -616,23 +621,80 @@ KF_HD T upd_fwd_joseph(State<T> &s, T ym, T zm, T s2) {
     }
     // A columns 0,1 (A = I - K H): rows 0,1 = R S^-1, rows 2..4 = -K
     T A[5][2];
-    A[0][0] = s2 * i00; A[0][1] = s2 * i01;
-    A[1][0] = s2 * i01; A[1][1] = s2 * i11;
+    A[0][0] = vy * i00; A[0][1] = vy * i01;
+    A[1][0] = vz * i01; A[1][1] = vz * i11;
     for (int j = 2; j < 5; j++) { A[j][0] = -K[j][0]; A[j][1] = -K[j][1]; }
     // B = A P  (A = [A_c | e_2 e_3 e_4 columns]):  B_ij = A_i0 P_0j + A_i1 P_1j + [i>=2] P_ij
     T B[5][5];
     for (int i = 0; i < 5; i++)
         for (int j = 0; j < 5; j++) B[i][j] = A[i][0] * s.P[0][j] + A[i][1] * s.P[1][j] + (i >= 2 ? s.P[i][j] : T(0));
     for (int j = 0; j < 5; j++) s.p[j] += K[j][0] * r0 + K[j][1] * r1;
-    // P_new = B A^T + s2 K K^T  (lower triangle, mirrored)
+    // P_new = B A^T + K R K^T  (lower triangle, mirrored)
     for (int i = 0; i < 5; i++)
         for (int j = 0; j <= i; j++) {
             const T v = B[i][0] * A[j][0] + B[i][1] * A[j][1] + (j >= 2 ? B[i][j] : T(0)) +
-                        s2 * (K[i][0] * K[j][0] + K[i][1] * K[j][1]);
+                        vy * K[i][0] * K[j][0] + vz * K[i][1] * K[j][1];
             s.P[i][j] = v;
             s.P[j][i] = v;
         }
     return chi2;
+}
+
+}  // namespace kf
+
+namespace kf {
+
+// Scalar measurement m of state component i with variance R (plain symmetric form):
+// u = P e_i, S = P_ii + R, r = m - p_i; p <- p + u r/S, P <- P - u u^T/S, chi2 += r^2/S.
+template <class T>
+KF_HD T upd1_fwd(State<T> &s, int i, T m, T R) {
+    T u[5];
+    for (int j = 0; j < 5; j++) u[j] = s.P[j][i];
+    const T S = u[i] + R;
+    const T iS = T(1) / S;
+    const T r = m - s.p[i];
+    const T g = r * iS;
+    for (int j = 0; j < 5; j++) s.p[j] += u[j] * g;
+    for (int a = 0; a < 5; a++)
+        for (int b = 0; b <= a; b++) {
+            const T v = s.P[a][b] - u[a] * u[b] * iS;
+            s.P[a][b] = v;
+            s.P[b][a] = v;
+        }
+    return r * g;
+}
+
+// Adjoint of upd1_fwd with d(chi2) = 1; `s` is the state before the update, `a` the adjoint after
+// it (overwritten with the adjoint before it).  The measured value is a constant.
+template <class T>
+KF_HD void upd1_bwd(const State<T> &s, int i, T m, T R, Adj<T> &a) {
+    T u[5];
+    for (int j = 0; j < 5; j++) u[j] = s.P[j][i];
+    const T S = u[i] + R;
+    const T iS = T(1) / S;
+    const T r = m - s.p[i];
+    const T g = r * iS;
+    // p' = p + u g ; chi2 = r g ; P' = P - u u^T / S
+    T gb = T(0), uGu = T(0);
+    T Gu[5];
+    for (int j = 0; j < 5; j++) {
+        gb += a.p[j] * u[j];
+        T acc = T(0);
+        for (int k = 0; k < 5; k++) acc += a.G[j][k] * u[k];
+        Gu[j] = acc;
+        uGu += u[j] * acc;
+    }
+    T ub[5];
+    for (int j = 0; j < 5; j++) ub[j] = a.p[j] * g - T(2) * Gu[j] * iS;
+    const T rb = gb * iS + T(2) * g;                 // from g = r/S and chi2 = r^2/S
+    const T Sb = -gb * g * iS - g * g + uGu * iS * iS;   // d/dS of g = r/S, chi2 = r^2/S, u u^T/S
+    // u = P e_i (symmetric split), S = P_ii + R, r = m - p_i
+    for (int j = 0; j < 5; j++) {
+        a.G[j][i] += T(0.5) * ub[j];
+        a.G[i][j] += T(0.5) * ub[j];
+    }
+    a.G[i][i] += Sb;
+    a.p[i] -= rb;
 }
 
 }  // namespace kf

@@ -351,10 +351,13 @@ int tpc_track_batch(tpc_ctx *c, const tpc_clusters *in, tpc_tracks *out, const t
 }
 
 int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, const double *theta,
-                   const float *weight, double *sum_chi2, double *grad, void *stream) {
+                   const float *weight, const float *anchor, int32_t error_model, double *sum_chi2, double *grad,
+                   void *stream) {
     if (!c || !theta || !sum_chi2 || !trk || !trk->trk_off || !trk->trk_hits || !trk->n_tracks ||
         trk->cap_tracks < 1)
         return TPC_ERR_INVALID_ARG;
+    if (anchor && (reinterpret_cast<uintptr_t>(anchor) & 15u)) return TPC_ERR_INVALID_ARG;
+    if (error_model != TPC_ERRORS_FIXED && error_model != TPC_ERRORS_RAW) return TPC_ERR_INVALID_ARG;
     int rc = validate_in(c, in);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -365,7 +368,7 @@ int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, co
     TPC_CUDA(cudaMemcpyAsync(W.counters + CNT_NTRACKS, trk->n_tracks, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     launch_pack_hits(W, s);
     if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[1], s));
-    launch_refit_grad_fit(W, theta, weight, grad != nullptr, c->ck, c->rec, c->order, c->lhist, s);
+    launch_refit_grad_fit(W, theta, weight, anchor, error_model, grad != nullptr, c->ck, c->rec, c->order, c->lhist, s);
     if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[2], s));
     launch_refit_grad_reduce(W, sum_chi2, grad, c->rec, c->part, s);
     if (prof) {
@@ -460,6 +463,7 @@ int tpc_debug_copy(tpc_ctx *c, int32_t what, void *dst, int64_t dst_bytes, void 
         case 8: src = w.seg_n; bytes = C * 4; break;
         case 9: src = w.next; bytes = C * 4; break;
         case 10: src = w.counters; bytes = 16 * 4; break;
+        case 11: src = c->rec; bytes = (size_t)refit_rec_words((int)(C + 1)) * 4; break;
         default: return TPC_ERR_INVALID_ARG;
     }
     if (dst_bytes < 0) return TPC_ERR_INVALID_ARG;

@@ -161,8 +161,8 @@ void launch_follow(const Work &W, cudaStream_t s);
 void launch_select(const Work &W, cudaStream_t s);
 void launch_merge(const Work &W, cudaStream_t s);
 void launch_refit(const Work &W, const float *theta, cudaStream_t s);
-void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, bool grad, float *ck, float *rec,
-                           int32_t *order, int32_t *hist, cudaStream_t s);
+void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
+                           bool grad, float *ck, float *rec, int32_t *order, int32_t *hist, cudaStream_t s);
 void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,
                               cudaStream_t s);
 int refit_ck_words(int cap_hits, int cap_tracks);

@@ -339,6 +339,60 @@ def calib_event(seed=1005, n_tracks=20000):
                        theta=calib_theta(seed))
 
 
+# Resolutions of the reference track at the vertex (inner-tracker-like): vertex point, z0, tan
+# lambda, relative q/pT.
+REF_SIGMA_V = 0.01
+REF_SIGMA_Z0 = 0.01
+REF_SIGMA_TL = 1e-3
+REF_SIGMA_QPT_REL = 0.01
+
+
+def vertex_references(ev: Event, trk_off, trk_hits, seed=1006, purity=0.9, smear=True, max_first_row=8,
+                      min_hits=30):
+    """Reference measurements at the vertex for reconstructed tracks, as float64 [T, 8] in the
+    layout of the refit's anchor input: (sigma_v, z0, sigma_z0, tan lambda, sigma_tl, q/pT,
+    sigma_qpt, 0).  A track is matched to the generating particle that holds at least `purity` of
+    its hits, provided the track runs along the particle's outgoing path (the particle's path
+    length from the vertex increases along the track's hit order; the returning leg of a looper
+    points away from the vertex and gets no reference) and the particle's direction at the vertex
+    is within |sin phi| < 0.9 of the first hit's sector frame.  As in a matching at the inner wall
+    of the TPC, only tracks that start within the first `max_first_row` pad rows and have at least
+    `min_hits` hits are matched.  The reference values are that particle's
+    (z0 = 0, tan lambda = sinh eta, q/pT) smeared with seeded Gaussian noise (exact values if smear
+    is False).  Unmatched tracks get a zero record (no reference)."""
+    trk_off = np.asarray(trk_off)
+    trk_hits = np.asarray(trk_hits)
+    nt = trk_off.shape[0] - 1
+    rng = np.random.default_rng(seed)
+    noise = rng.normal(0.0, 1.0, size=(nt, 3)) if smear else np.zeros((nt, 3))
+    out = np.zeros((nt, 8))
+    for t in range(nt):
+        lab = ev.mc_track[trk_hits[trk_off[t]:trk_off[t + 1]]]
+        lab = lab[lab >= 0]
+        if lab.size == 0:
+            continue
+        vals, cnt = np.unique(lab, return_counts=True)
+        p = int(vals[np.argmax(cnt)])
+        if cnt.max() < purity * (trk_off[t + 1] - trk_off[t]):
+            continue
+        own = trk_hits[trk_off[t]:trk_off[t + 1]]
+        if own.size < min_hits or int(ev.row[own[0]]) > max_first_row:
+            continue
+        path = ev.true_s[own[ev.mc_track[own] == p]]
+        if path.size < 2 or not np.all(np.diff(path) > 0):
+            continue
+        # the step to the vertex runs in the frame of the first hit's sector: keep it well inside
+        # the local parametrisation (|sin phi| < 0.9 at the vertex)
+        if abs(math.sin(ev.trk_phi0[p] - sector_alpha(int(ev.sector[own[0]])))) >= 0.9:
+            continue
+        tl = math.sinh(ev.trk_eta[p])
+        qpt = ev.trk_q[p] / ev.trk_pt[p]
+        sq = REF_SIGMA_QPT_REL * abs(qpt)
+        out[t] = (REF_SIGMA_V, REF_SIGMA_Z0 * noise[t, 0], REF_SIGMA_Z0, tl + REF_SIGMA_TL * noise[t, 1],
+                  REF_SIGMA_TL, qpt + sq * noise[t, 2], sq, 0.0)
+    return out
+
+
 @dataclasses.dataclass
 class Batch:
     pad_fp: np.ndarray

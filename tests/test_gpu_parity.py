@@ -126,12 +126,13 @@ def _weights(f):
     return ((f["ndf"] > 0) & (f["chi2"] < GOOD_CHI2_NDF * np.maximum(f["ndf"], 1))).astype(np.float64)
 
 
-def _refit_sum_grad(ctx, cl, tr, theta, w):
+def _refit_sum_grad(ctx, cl, tr, theta, w, ref=None, model=0):
     th = torch.tensor(theta, dtype=torch.float64, device="cuda")
     wt = torch.tensor(w, dtype=torch.float32, device="cuda")
+    an = torch.tensor(ref, dtype=torch.float32, device="cuda") if ref is not None else None
     s = torch.empty(1, dtype=torch.float64, device="cuda")
     g = torch.empty(73, dtype=torch.float64, device="cuda")
-    ctx.tpc_refit_grad(cl, tr, th, s, g, wt)
+    ctx.tpc_refit_grad(cl, tr, th, s, g, wt, an, model)
     assert ctx.tpc_sync_status() == 0
     return float(s.item()), g.cpu().numpy()
 
@@ -151,8 +152,13 @@ def _block_err(g, ref, ns=36):
     return np.array(out)
 
 
-@pytest.mark.parametrize("which", ["nominal", "injected"])
+@pytest.mark.parametrize("which", ["nominal", "injected", "anchored-nominal", "anchored-injected",
+                                   "raw-anchored-nominal", "raw-anchored-injected"])
 def test_adjoint_gradient_matches_fp64_central_differences(ctx, which):
+    """The anchored variants add the reference measurements at the vertex (step to x = 0, vertex
+    point, reference z0, tan lambda and q/pT); both sides take the same float32 reference values.
+    The raw variants take the measurement errors in the raw coordinates (variances that depend on
+    theta, so the adjoint also runs through the measurement covariance)."""
     th_star = synth.calib_theta(1005)
     ev = synth.make_event(synth.EventConfig(n_tracks=3000, noise_frac=0.3, looper_frac=0.1, seed=77,
                                             theta=th_star))
@@ -161,10 +167,17 @@ def test_adjoint_gradient_matches_fp64_central_differences(ctx, which):
     cl = _gpu.clusters_of(ev)
     g = _gpu.run(ctx, cl)
     _compare_tracks(g, o, ev.n_clusters)
-    theta = synth.theta_nominal() if which == "nominal" else th_star
-    s_gpu, g_gpu = _refit_sum_grad(ctx, cl, g["tracks_obj"], theta, w)
-    s_ref = O.chi2_total(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w)
-    g_ref = O.grad_fd(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w)
+    theta = synth.theta_nominal() if which.endswith("nominal") else th_star
+    model = 1 if which.startswith("raw") else 0
+    ref = None
+    if "anchored" in which:
+        ref = synth.vertex_references(ev, o["trk_off"], o["trk_hits"]).astype(np.float32).astype(np.float64)
+        assert (ref[:, 0] > 0).sum() > 0.5 * len(ref)
+    s_gpu, g_gpu = _refit_sum_grad(ctx, cl, g["tracks_obj"], theta, w, ref, model)
+    s_ref = O.chi2_total(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w, ref=ref,
+                         mode=model)
+    g_ref = O.grad_fd(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w, ref=ref,
+                      mode=model)
     print("sum chi2 gpu %.6f oracle %.6f (%d of %d tracks)" % (s_gpu, s_ref, int(w.sum()), len(w)))
     assert s_gpu == pytest.approx(s_ref, rel=1e-4)
     err = _grad_err(g_gpu, g_ref)

@@ -243,6 +243,85 @@ def test_fit_matches_least_squares_optimum():
 
 
 # ---------------------------------------------------------------------------------------------
+# Reference measurements at the vertex (identifiability of the calibration)
+# ---------------------------------------------------------------------------------------------
+
+def _vertex_truth(ev, p, k):
+    """Generating state at the vertex in the frame of sector k: (0, 0, sin(phi0 - alpha_k), tan
+    lambda, q/pT)."""
+    alpha = math.radians(((k % 18) + 0.5) * 20.0)
+    return np.array([0.0, 0.0, math.sin(ev.trk_phi0[p] - alpha), math.sinh(ev.trk_eta[p]),
+                     ev.trk_q[p] / ev.trk_pt[p]])
+
+
+def test_fit_with_exact_vertex_references_reproduces_the_generating_helix():
+    """Exact points and exact reference values: after the step to the vertex and the reference
+    updates, the state is the generating one at x = 0 and chi2 stays zero.  A reference applied to
+    the wrong state component, or a wrong step to the vertex, leaves a residual."""
+    ev = _events.noise_free(n_tracks=300, seed=23)
+    worst, n = 0.0, 0
+    for p, idx in _outgoing_tracks(ev, max_tracks=150):
+        exp = _vertex_truth(ev, p, int(ev.sector[idx[0]]))
+        ref = np.array([0.01, 0.0, 0.01, exp[3], 1e-3, exp[4], 0.01 * abs(exp[4]), 0.0])
+        ok, par, xref, cov, chi2 = O.fit_xyz(ev.sector[idx], ev.true_xyz[idx], ref=ref)
+        if not ok:
+            continue
+        n += 1
+        assert xref == 0.0
+        assert chi2 < 1e-10, chi2
+        worst = max(worst, (np.abs(par - exp) / np.maximum(np.abs(exp), [1.0, 1.0, 1e-2, 1e-2, 1e-2])).max())
+    assert n > 100
+    assert worst < 1e-8, worst
+
+
+def test_vertex_references_match_least_squares_optimum():
+    """Smeared points and smeared reference values: the filter with the vertex step and the
+    reference updates reaches the least-squares optimum of the independent closed-form helix with
+    the extra residuals (vertex point, z0, tan lambda, q/pT), and chi2 agrees to 0.05.  The step's z
+    row keeps the chord term only (the reading of the fit's Jacobian), which over the long step to
+    the vertex leaves up to ~0.15 standard errors in tan lambda on strongly bent tracks: the bound
+    is 0.25 standard errors per track and 0.01 for the median, while a wrong sign or component
+    in any reference term moves every track by about one standard error."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    ev = _events.noise_free(n_tracks=300, seed=43, single_sector=True)
+    rng = np.random.default_rng(44)
+    c0 = np.array([1.0, 1.0, 0.01, 0.01, 1.0])
+    dev = []
+    for p, idx in _outgoing_tracks(ev, min_hits=40, max_tracks=40):
+        xyz = ev.true_xyz[idx].copy()
+        xyz[:, 1:] += rng.normal(0, 0.01, (len(idx), 2))
+        tv = _vertex_truth(ev, p, int(ev.sector[idx[0]]))
+        sg = np.array([0.01, 0.01, 1e-3, 0.01 * abs(tv[4])])
+        meas = np.array([0.0, tv[1], tv[3], tv[4]]) + rng.normal(0, 1, 4) * sg
+        meas[0] = 0.0
+        ref = np.array([sg[0], meas[1], sg[1], meas[2], sg[2], meas[3], sg[3], 0.0])
+        ok, par, xref, cov, chi2 = O.fit_xyz(ev.sector[idx], xyz, ref=ref)
+        if not ok:
+            continue
+        e = xyz[-1]
+        prior = _seed_prior(xyz)
+
+        def resid(v):
+            yv, zv = _helix_predict(v, e[0], xyz[:, 0])
+            y0, z0 = _helix_predict(v, e[0], np.array([0.0]))
+            extra = [y0[0] / sg[0], z0[0] / sg[0], (z0[0] - meas[1]) / sg[1], (v[3] - meas[2]) / sg[2],
+                     (v[4] - meas[3]) / sg[3]]
+            return np.concatenate([(yv - xyz[:, 1]) / 0.1, (zv - xyz[:, 2]) / 0.1, (v - prior) / np.sqrt(c0), extra])
+
+        sol = scipy_opt.least_squares(resid, prior, xtol=1e-15, ftol=1e-15, gtol=1e-15, method="lm")
+        v = sol.x
+        y0, z0 = _helix_predict(v, e[0], np.array([0.0]))
+        vert = np.array([y0[0], z0[0], v[2] + KB * v[4] * (0.0 - e[0]), v[3], v[4]])
+        sig = np.sqrt(np.diag(O.cov_matrix(cov)))
+        dev.append(np.abs(par - vert) / sig)
+        assert chi2 == pytest.approx(float(np.sum(resid(v) ** 2)), abs=0.05)
+    dev = np.array(dev)
+    assert len(dev) >= 20
+    assert np.all(dev.max(axis=0) < 0.25), dev.max(axis=0)
+    assert np.all(np.median(dev, axis=0) < 0.01), np.median(dev, axis=0)
+
+
+# ---------------------------------------------------------------------------------------------
 # S2 / S3 links: brute force on tiny sectors
 # ---------------------------------------------------------------------------------------------
 
@@ -490,3 +569,67 @@ def test_fd_gradient_vanishes_at_the_injected_calibration():
     assert abs(g_star @ delta) < 0.05 * abs(g_nom @ delta)
     g_half = O.grad_fd(ev.pad_fp, ev.time_fp, ev.bin_off, off, hits, th0, h=(5e-7, 5e-5, 5e-5))
     np.testing.assert_allclose(g_half, g_nom, rtol=1e-5, atol=1e-6 * np.abs(g_nom).max())
+
+
+def test_vertex_references_remove_the_blind_directions():
+    """Without references the objective cannot see a common z shift of all clusters of one side
+    (every helix absorbs it in z0); with the vertex point and the reference track's z0 it can.
+    With exact references on unsmeared clusters, the anchored objective still has its minimum at
+    the injected theta*: its value stays at quantisation level and its gradient vanishes there."""
+    th = synth.calib_theta(1005)
+    ev = _events.noise_free(n_tracks=300, seed=51, theta=th)
+    r = O.track_event(ev.pad_fp, ev.time_fp, ev.bin_off)
+    off, hits = r["trk_off"], r["trk_hits"]
+    ref = synth.vertex_references(ev, off, hits, smear=False)
+    assert (ref[:, 0] > 0).sum() > 0.8 * len(ref)
+    args = (ev.pad_fp, ev.time_fp, ev.bin_off, off, hits)
+    shift = th.copy()
+    shift[1:19] += 0.05                                     # all sectors of the A side, +0.5 mm
+    c0 = O.chi2_total(*args, th)
+    c1 = O.chi2_total(*args, shift)
+    assert c1 == pytest.approx(c0, rel=1e-6, abs=1e-6)
+    r0 = O.chi2_total(*args, th, ref=ref)
+    r1 = O.chi2_total(*args, shift, ref=ref)
+    n_meas = 2 * len(hits)
+    assert r0 < 2.0 * n_meas * (1.0 / 128 ** 2 / 12) / 0.01 + 1.0
+    n_side = int(((ref[:, 0] > 0) & (ev.sector[hits[off[:-1]]] < 18)).sum())
+    # every referenced track of the shifted side sees a 0.05 cm offset between its extrapolated z
+    # at the vertex (track error ~0.03 cm) and two 0.01 cm references: more than 1 in chi2 each
+    assert r1 - r0 > 1.0 * n_side
+    th0 = synth.theta_nominal()
+    g_star = O.grad_fd(*args, th, ref=ref)
+    g_nom = O.grad_fd(*args, th0, ref=ref)
+    delta = th - th0
+    assert abs(g_star @ delta) < 0.05 * abs(g_nom @ delta)
+
+
+def _z_scale(theta, eps):
+    """theta after a common scale (1 + eps) of every calibrated z about z = 0: s_vd and d_k scale,
+    and d_k moves by +-z_max*eps (A/C side)."""
+    t = np.array(theta, np.float64)
+    out = t.copy()
+    out[0] = (1 + eps) * t[0]
+    out[1:19] = (1 + eps) * t[1:19] + 250.0 * eps
+    out[19:37] = (1 + eps) * t[19:37] - 250.0 * eps
+    return out
+
+
+def test_raw_error_model_is_blind_to_a_rescaling_of_the_data():
+    """Clusters smeared in the raw coordinates: with fixed calibrated errors (mode 0) the sum of
+    chi2 drops when theta rescales every z towards z = 0 (the residuals shrink with the data,
+    about 2 eps of the z part of chi2), while with the raw errors carried through the
+    transformation (mode 1) chi2 does not change to first order.  At the nominal theta both modes
+    are the same function."""
+    th = synth.calib_theta(1005)
+    ev = synth.make_event(synth.EventConfig(n_tracks=300, noise_frac=0.0, seed=61, theta=th))
+    r = O.track_event(ev.pad_fp, ev.time_fp, ev.bin_off)
+    args = (ev.pad_fp, ev.time_fp, ev.bin_off, r["trk_off"], r["trk_hits"])
+    th0 = synth.theta_nominal()
+    assert O.chi2_total(*args, th0, mode=1) == O.chi2_total(*args, th0, mode=0)
+    eps = 1e-3
+    f0 = O.chi2_total(*args, th, mode=0)
+    d0 = O.chi2_total(*args, _z_scale(th, eps), mode=0) - O.chi2_total(*args, _z_scale(th, -eps), mode=0)
+    d1 = O.chi2_total(*args, _z_scale(th, eps), mode=1) - O.chi2_total(*args, _z_scale(th, -eps), mode=1)
+    # mode 0: d0 ~ 4 eps chi2_z with chi2_z about half of f0
+    assert d0 > 1.0 * eps * f0, (d0, f0)
+    assert abs(d1) < 0.02 * d0, (d1, d0)
