@@ -123,9 +123,15 @@ __device__ __forceinline__ float nominal_z(const DevGeom &G, const HitRaw &h) {
     return side * (G.z_max - (float)h.Z * G.lsb);
 }
 
+// Prior covariance of the seed: sigma = 1 cm (y, z), 0.1 (sin phi, tan lambda), 1 c/GeV (q/pT).
+__device__ __constant__ const float C0[5] = {1.f, 1.f, 0.01f, 0.01f, 1.f};
+__device__ __constant__ const float SQRT_C0[5] = {1.f, 1.f, 0.1f, 0.1f, 1.f};
+
 // Seed: sin phi, tan lambda, q/pT from the circle through the nominal first, middle and last hit
-// (theta-independent); position = the last hit under theta; references = the last hit.
-__device__ bool seed_track(const Work &W, const DevGeom &G, const float *th, int off, int n, kf::State<float> &s) {
+// (theta-independent); position = the last hit under theta; references = the last hit.  The caller
+// sets the prior covariance.
+template <class St>
+__device__ bool seed_track(const Work &W, const DevGeom &G, const float *th, int off, int n, St &s) {
     const HitRaw e = hit_raw(W, off + n - 1), a = hit_raw(W, off), b = hit_raw(W, off + (n - 1) / 2);
     float ax, ay, bx, by, ex, ey;
     nominal_rel(G, a, e, ax, ay);
@@ -141,9 +147,6 @@ __device__ bool seed_track(const Work &W, const DevGeom &G, const float *th, int
     s.yref = he.f.yn;
     s.zref = he.f.zn;
     s.frame = e.k;
-    const float c0[5] = {1.f, 1.f, 0.01f, 0.01f, 1.f};
-    for (int i = 0; i < 5; i++)
-        for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? c0[i] : 0.f;
     return true;
 }
 
@@ -169,16 +172,18 @@ __global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
             set_status(W, ST_CAPACITY);
             n = 0;
         }
-        kf::State<float> s;
+        kf::SqrtState<float> s;
         s.x = 0.f;
         s.rref = 0;
         s.frame = 0;
         s.yref = s.zref = 0.f;
+        for (int i = 0; i < 5; i++)
+            for (int j = 0; j < 5; j++) s.S[i][j] = i == j ? SQRT_C0[i] : 0.f;
         float chi2 = 0.f;
         bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
         for (int i = n - 1; ok && i >= 0; i--) {
             const HitT m = transform(G, th, ns, hit_raw(W, off + i));
-            ok = kf::step_fwd(s, m.f, fg.g, chi2);
+            ok = kf::sqrt_step(s, m.f, fg.g, chi2);
         }
         s.p[0] += s.yref;
         s.p[1] += s.zref;
@@ -186,7 +191,11 @@ __global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
         for (int i = 0; i < 5; i++) W.par[5 * t + i] = ok ? s.p[i] : 0.f;
         int m = 0;
         for (int i = 0; i < 5; i++)
-            for (int j = 0; j <= i; j++) W.cov[15 * t + m++] = ok ? s.P[i][j] : 0.f;
+            for (int j = 0; j <= i; j++) {
+                float v = 0.f;
+                for (int k = 0; k < 5; k++) v += s.S[i][k] * s.S[j][k];
+                W.cov[15 * t + m++] = ok ? v : 0.f;
+            }
         W.xref[t] = ok ? xabs : 0.f;
         W.chi2[t] = ok ? chi2 : 0.f;
         W.ndf[t] = ok ? 2 * n - 5 : 0;
@@ -335,6 +344,8 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
         s.rref = 0;
         s.frame = 0;
         s.yref = s.zref = 0.f;
+        for (int i = 0; i < 5; i++)
+            for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? C0[i] : 0.f;
         float chi2 = 0.f;
         bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
         for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q

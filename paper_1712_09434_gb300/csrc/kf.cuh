@@ -196,8 +196,8 @@ struct PropV {   // forward intermediates of one propagation step
     T F02, F04, F12, F13, F14, F24;
 };
 
-template <class T>
-KF_HD bool prop_vals(const State<T> &s, T dx, T kB, T smax, PropV<T> &v) {
+template <class T, class St>
+KF_HD bool prop_vals(const St &s, T dx, T kB, T smax, PropV<T> &v) {
     const T sn = s.p[2], tl = s.p[3], q = s.p[4];
     v.dx = dx;
     v.C = kB * q;
@@ -695,6 +695,118 @@ KF_HD void upd1_bwd(const State<T> &s, int i, T m, T R, Adj<T> &a) {
     }
     a.G[i][i] += Sb;
     a.p[i] -= rb;
+}
+
+}  // namespace kf
+
+namespace kf {
+
+// ---- square-root form of the forward filter ----------------------------------------------------
+// The same filter with the covariance carried as a square root, P = S S^T (S a general 5x5
+// matrix).  A linear map J acts as S <- J S; a scalar measurement of component i with variance R
+// is Potter's square-root update: phi = S^T e_i, a = 1/(phi.phi + R), g = 1/(1 + sqrt(a R)),
+// K = a S phi, S <- S - g a (S phi) phi^T, which is P <- P - K e_i^T P exactly.  The (y, z)
+// measurement with diagonal R is processed as two scalar updates (the same posterior and the same
+// total chi2 as the joint update).  In FP32 the square root halves the digits the covariance loses
+// to its condition number.
+template <class T>
+struct SqrtState {
+    T x;
+    T p[5];
+    T S[5][5];
+    int frame;
+    int rref;
+    T yref, zref;
+};
+
+template <class T>
+KF_HD bool sqrt_rot(SqrtState<T> &s, T ca, T sa, T kB, T cmin) {
+    const T sn = s.p[2];
+    const T cs = k_sqrt(T(1) - sn * sn);
+    const T x1 = s.x * ca + s.p[0] * sa;
+    const T y1 = -s.x * sa + s.p[0] * ca;
+    const T sn1 = sn * ca - cs * sa;
+    const T cs1 = cs * ca + sn * sa;
+    if (!(cs1 > cmin)) return false;
+    const T C = kB * s.p[4];
+    const T j00 = cs / cs1, j10 = -s.p[3] * sa / cs1, j20 = -C * sa, j22 = cs1 / cs;
+    for (int j = 0; j < 5; j++) {
+        const T s0 = s.S[0][j];
+        s.S[0][j] = j00 * s0;
+        s.S[1][j] = j10 * s0 + s.S[1][j];
+        s.S[2][j] = j20 * s0 + j22 * s.S[2][j];
+    }
+    s.x = x1;
+    s.p[0] = y1;
+    s.p[2] = sn1;
+    return true;
+}
+
+template <class T>
+KF_HD bool sqrt_prop(SqrtState<T> &s, T dx, T kB, T smax, T dyref, T dzref) {
+    PropV<T> v;
+    if (!prop_vals(s, dx, kB, smax, v)) return false;
+    for (int j = 0; j < 5; j++) {
+        const T s2 = s.S[2][j], s3 = s.S[3][j], s4 = s.S[4][j];
+        s.S[0][j] += v.F02 * s2 + v.F04 * s4;
+        s.S[1][j] += v.F12 * s2 + v.F13 * s3 + v.F14 * s4;
+        s.S[2][j] += v.F24 * s4;
+    }
+    s.p[0] += v.dx * v.T_ - dyref;
+    s.p[1] += s.p[3] * v.arc - dzref;
+    s.p[2] = v.s2;
+    return true;
+}
+
+template <class T>
+KF_HD T sqrt_upd1(SqrtState<T> &s, int i, T m, T R) {
+    T phi[5], Sphi[5];
+    T pp = T(0);
+    for (int j = 0; j < 5; j++) {
+        phi[j] = s.S[i][j];
+        pp += phi[j] * phi[j];
+    }
+    for (int a = 0; a < 5; a++) {
+        T v = T(0);
+        for (int j = 0; j < 5; j++) v += s.S[a][j] * phi[j];
+        Sphi[a] = v;
+    }
+    const T alpha = T(1) / (pp + R);
+    const T gamma = T(1) / (T(1) + k_sqrt(alpha * R));
+    const T r = m - s.p[i];
+    const T ar = alpha * r, ga = gamma * alpha;
+    for (int a = 0; a < 5; a++) {
+        s.p[a] += Sphi[a] * ar;
+        for (int b = 0; b < 5; b++) s.S[a][b] -= ga * Sphi[a] * phi[b];
+    }
+    return r * ar;
+}
+
+// One step to hit h in square-root form (same geometry as step_fwd).
+template <class T>
+KF_HD bool sqrt_step(SqrtState<T> &s, const FHit<T> &h, const Geo<T> &g, T &chi2) {
+    if (h.k != s.frame) {
+        const int m = rot_index(h.k, s.frame, g.half);
+        s.x = g.xr[s.rref] + s.x;
+        s.p[0] = s.yref + s.p[0];
+        if (!sqrt_rot(s, g.rot_c[m], g.rot_s[m], g.kB, g.cmin)) return false;
+        s.x = s.x - g.xr[h.r];
+        s.p[0] = s.p[0] - h.yn;
+        s.p[1] = s.p[1] + (s.zref - h.zn);
+        s.rref = h.r;
+        s.yref = h.yn;
+        s.zref = h.zn;
+        s.frame = h.k;
+    }
+    const T dx = T(h.r - s.rref) * g.pitch + (h.xl - s.x);
+    if (!sqrt_prop(s, dx, g.kB, g.smax, h.yn - s.yref, h.zn - s.zref)) return false;
+    s.x = h.xl;
+    s.rref = h.r;
+    s.yref = h.yn;
+    s.zref = h.zn;
+    chi2 += sqrt_upd1(s, 0, h.yc, h.vy);
+    chi2 += sqrt_upd1(s, 1, h.zc, h.vz);
+    return true;
 }
 
 }  // namespace kf

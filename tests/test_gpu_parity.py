@@ -83,7 +83,7 @@ def _par_err(gp, op, ocov):
 def test_refit_parameters_match_fp64_oracle(ctx, name):
     """Tracks with a consistent hit set (oracle chi2/ndf < 5) agree to 1e-4.  Tracks whose residuals
     are many sigma (impure candidates, chi2/ndf >= 5, 1-10 % of the tracks) amplify FP32 rounding
-    through the linearisation point: they are held to 1e-2 and their statistics are printed."""
+    through the linearisation point: they are held to 1e-3 and their statistics are printed."""
     ev = _events.event(name)
     o = O.track_event(ev.pad_fp, ev.time_fp, ev.bin_off)
     g = _gpu.run(ctx, _gpu.clusters_of(ev))
@@ -102,7 +102,7 @@ def test_refit_parameters_match_fp64_oracle(ctx, name):
         bad_err.max(axis=0) if len(bad_err) else None))
     assert np.all(err.max(axis=0) < PAR_RTOL), err.max(axis=0)
     if len(bad_err):
-        assert np.all(bad_err.max(axis=0) < 1e-2)
+        assert np.all(bad_err.max(axis=0) < 1e-3)
     np.testing.assert_allclose(g["xref"][both], f["xref"][both], rtol=1e-6, atol=1e-4)
     # chi2 is a sum of up to 300 squared residuals: its FP32 error grows with the residuals, so
     # consistent tracks (chi2/ndf < 2) are held to 2e-4 and the rest of the good set to 2e-3
@@ -113,12 +113,14 @@ def test_refit_parameters_match_fp64_oracle(ctx, name):
         chi_err[tight].max(), tight.sum(), chi_err[good & ~tight].max() if (good & ~tight).any() else 0.0))
     assert chi_err[tight].max() < 2e-4
     assert chi_err[good].max() < 2e-3
-    # covariance diagonal: the filter shrinks a variance from its prior by up to ~1e4-1e5, and an
-    # FP32 update keeps about eps * (prior / posterior) of relative accuracy (6e-8 * 1e5 = 6e-3)
+    # covariance diagonal: the filter shrinks a variance from its prior by up to ~1e4-1e5; a
+    # covariance update in FP32 keeps about eps * (prior / posterior) of relative accuracy
+    # (6e-8 * 1e5 = 6e-3), its square root (the refit carries P = S S^T) about
+    # eps * sqrt(prior / posterior) per update, ~1e-5 after 159 updates: held to 1e-3
     cerr = np.abs(g["cov"][good][:, [0, 2, 5, 9, 14]] - f["cov"][good][:, [0, 2, 5, 9, 14]]) / \
         np.abs(f["cov"][good][:, [0, 2, 5, 9, 14]])
     print("cov diag max rel err", cerr.max(axis=0), "p99", np.percentile(cerr, 99, axis=0))
-    assert cerr.max() < 1e-2
+    assert cerr.max() < 1e-3
 
 
 def _weights(f):
