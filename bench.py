@@ -363,7 +363,8 @@ def finish_native(args, res, world):
     plain_value = res["n_clusters"] / (res["ms_plain"] * 1e-3)
     e2e_value = n_cl_total / (res["ms_e2e"] * 1e-3)
     traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    # DRAM bytes per launch of the dominant kernel from an ncu capture (null if none matches)
+    prof_path = os.path.join(ROOT, "profiles", "k_%s_batch64_traffic.json" % dom)
     if os.path.exists(prof_path):
         tj = json.load(open(prof_path))
         if tj.get("stage") == dom and tj.get("workload") == WORKLOAD:
