@@ -384,6 +384,9 @@ def finish_native(args, res, world):
                     "tracks": res["n_tracks_c5"]},
         "calibration": res["calib"],
         "stage_ms": stage_ms,
+        "stage_algorithmic_gbs": {k: byts[k] / (stage_ms[k] * 1e-3) / 1e9 for k in stage_ms if k in byts and stage_ms[k] > 0},
+        "units": {"clusters": res["n_clusters"], "chains": res["n_chains"], "candidate_hits": res["cand_hits"],
+                  "tracks": res["n_tracks"], "track_hits": res["n_hits"]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes": byts[dom]},
