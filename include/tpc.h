@@ -87,8 +87,10 @@ typedef struct {
 } tpc_tracks;
 
 /* Launch shape of the tunable kernels (0 = library default).  Index: 0 grid, 1 links, 2 chains,
- * 3 follow, 4 select, 5 merge, 6 refit, 7 refit_grad.  block = threads per CTA (multiple of 32),
- * ctas_per_sm = persistent CTAs per SM, chunk = work items taken per queue grab. */
+ * 3 follow, 4 select, 5 merge, 6 refit, 7 refit_grad.  block = threads per CTA (multiple of 32, at
+ * most 256, 128, 256, 128, 1024, 512, 128, 128 by index), ctas_per_sm = CTAs per SM of the grid
+ * (<= 64), chunk = work items taken per queue grab (<= 64; used by the following).  Launch shapes
+ * never change results. */
 typedef struct {
     int32_t block[TPC_N_TUNE];
     int32_t ctas_per_sm[TPC_N_TUNE];
@@ -151,6 +153,11 @@ int tpc_track_batch(tpc_ctx *ctx, const tpc_clusters *in, tpc_tracks *out, const
 int tpc_refit_grad(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, const double *theta,
                    const float *weight, const float *anchor, int32_t error_model, double *sum_chi2, double *grad,
                    void *stream);
+
+/* Set the launch shapes that later calls of this context use when they pass none (tpc_track_event,
+ * tpc_refit_grad, and tpc_track_batch with tune == NULL); NULL restores the library defaults.
+ * The values are copied.  Errors: INVALID_ARG (a value outside the bounds of tpc_tuning). */
+int tpc_set_tuning(tpc_ctx *ctx, const tpc_tuning *tune);
 
 /* Wait for `stream` and return the device status word of the last calls (then clear it). */
 int tpc_sync_status(tpc_ctx *ctx, void *stream);

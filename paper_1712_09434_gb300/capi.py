@@ -74,6 +74,7 @@ def _load():
     lib.tpc_refit_grad.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp, i32,
                                    vp, vp, vp]
     lib.tpc_sync_status.argtypes = [vp, vp]
+    lib.tpc_set_tuning.argtypes = [vp, ctypes.POINTER(tpc_tuning)]
     lib.tpc_strerror.argtypes = [ctypes.c_int]
     lib.tpc_strerror.restype = ctypes.c_char_p
     lib.tpc_debug_copy.argtypes = [vp, i32, vp, i64, vp]
@@ -229,6 +230,10 @@ class Context:
         check(_lib.tpc_refit_grad(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(theta), _ptr(weight),
                                   _ptr(anchor), int(error_model), _ptr(sum_chi2), _ptr(grad), _stream(stream)),
               "tpc_refit_grad")
+
+    def tpc_set_tuning(self, tuning=None):
+        check(_lib.tpc_set_tuning(self.handle, ctypes.byref(tuning) if tuning is not None
+                                  else ctypes.POINTER(tpc_tuning)()), "tpc_set_tuning")
 
     def tpc_sync_status(self, stream=None):
         return _lib.tpc_sync_status(self.handle, _stream(stream))

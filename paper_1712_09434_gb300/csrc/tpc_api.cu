@@ -38,6 +38,9 @@ struct tpc_ctx {
     bool pipe_pending, refit_pending;
     double acc_ms[TPC_N_PIPE_STAGES + TPC_N_REFIT_STAGES];
     int acc_calls;
+    // launch shapes set by tpc_set_tuning (used when a call passes no tuning of its own)
+    tpc_tuning tune;
+    bool has_tune;
 };
 
 namespace {
@@ -133,7 +136,7 @@ int validate_out(const tpc_tracks *o) {
 }
 
 // largest block size each tunable kernel is compiled for (__launch_bounds__)
-const int kMaxBlock[TPC_N_TUNE] = {256, 128, 256, 128, 1024, 1024, 128, 128};
+const int kMaxBlock[TPC_N_TUNE] = {256, 128, 256, 128, 1024, 512, 128, 128};
 
 Work make_work(const tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *o, const tpc_tuning *tune) {
     Work w = c->ws;
@@ -161,6 +164,7 @@ Work make_work(const tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *o, co
     w.cap_tracks = o->cap_tracks < c->cap_chains ? o->cap_tracks : c->cap_chains;
     w.cap_hits = o->cap_hits < c->max_clusters + 1 ? o->cap_hits : c->max_clusters + 1;
     std::memset(&w.tune, 0, sizeof(w.tune));
+    if (!tune && c->has_tune) tune = &c->tune;
     if (tune) {
         for (int k = 0; k < TPC_N_TUNE; k++) {
             w.tune.block[k] = tune->block[k] > 0 && tune->block[k] % 32 == 0 && tune->block[k] <= kMaxBlock[k] ? tune->block[k] : 0;
@@ -295,6 +299,22 @@ void tpc_destroy(tpc_ctx *c) {
     if (c->dgeom) cudaFree(c->dgeom);
     if (c->theta0) cudaFree(c->theta0);
     delete c;
+}
+
+int tpc_set_tuning(tpc_ctx *c, const tpc_tuning *tune) {
+    if (!c) return TPC_ERR_INVALID_ARG;
+    if (tune) {
+        for (int k = 0; k < TPC_N_TUNE; k++)
+            if (tune->block[k] < 0 || tune->ctas_per_sm[k] < 0 || tune->chunk[k] < 0 ||
+                (tune->block[k] > 0 && (tune->block[k] % 32 != 0 || tune->block[k] > kMaxBlock[k])) ||
+                tune->ctas_per_sm[k] > 64 || tune->chunk[k] > 64)
+                return TPC_ERR_INVALID_ARG;
+        c->tune = *tune;
+        c->has_tune = true;
+    } else {
+        c->has_tune = false;
+    }
+    return TPC_OK;
 }
 
 int tpc_track_event(tpc_ctx *c, const tpc_clusters *in, tpc_tracks *out, void *stream) {

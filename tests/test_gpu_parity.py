@@ -255,3 +255,38 @@ def test_degenerate_inputs(ctx):
     o = O.track_event(ev1.pad_fp, ev1.time_fp, ev1.bin_off)
     g = _gpu.run(ctx, _gpu.clusters_of(ev1))
     _compare_tracks(g, o, ev1.n_clusters)
+
+
+def test_launch_shapes_do_not_change_results(ctx):
+    """Non-default launch shapes (tpc_set_tuning / tpc_track_batch tuning) give bit-identical
+    tracks, parameters, chi2 sums and gradients; out-of-range shapes are rejected."""
+    from paper_1712_09434_gb300 import capi, tune
+    cfgs = synth.batch_configs(n_events=4, seed0=2200)
+    for c in cfgs:
+        c.n_tracks = min(c.n_tracks, 2000)
+    b = synth.concat_events([synth.make_event(c) for c in cfgs])
+    cl = _gpu.clusters_of(b, b.n_events)
+    th = synth.theta_nominal()
+
+    def run_all():
+        g = _gpu.run(ctx, cl, n_events=b.n_events, batch=True)
+        s, gr = _refit_sum_grad(ctx, cl, g["tracks_obj"], th, np.ones(g["n_tracks"]))
+        return g, s, gr
+
+    ctx.tpc_set_tuning(None)
+    g0, s0, gr0 = run_all()
+    shapes = {"grid": (64, 8, 0), "links": (64, 4, 0), "chains": (128, 8, 0), "follow": (64, 4, 2),
+              "select": (256, 1, 0), "merge": (512, 4, 0), "refit": (64, 2, 0), "refit_grad": (64, 2, 0)}
+    ctx.tpc_set_tuning(tune.to_struct(shapes))
+    try:
+        g1, s1, gr1 = run_all()
+    finally:
+        ctx.tpc_set_tuning(None)
+    for k in ("trk_off", "trk_hits", "label", "par", "cov", "chi2", "ndf"):
+        np.testing.assert_array_equal(g0[k], g1[k], err_msg=k)
+    assert s0 == s1
+    np.testing.assert_array_equal(gr0, gr1)
+    bad = tune.to_struct({"links": (256, 4, 0)})            # above the kernel's 128 threads
+    with pytest.raises(capi.TpcError) as e:
+        ctx.tpc_set_tuning(bad)
+    assert e.value.code == capi.TPC_ERR_INVALID_ARG
