@@ -251,7 +251,7 @@ def run_native(args, rank, world):
     n_tracks, n_hits = res["n_tracks"], int(res["trk_off"][-1])
 
     out = {"ms_step": ms_all, "n_clusters": n_clusters, "n_clusters_all": n_cl_all, "n_tracks": n_tracks,
-           "n_hits": n_hits, "clocks": clk, "tuning": tuning_info}
+           "n_hits": n_hits, "clocks": clk, "tuning": tuning_info, "prof": prof}
     if args.only_step:
         return out
 
@@ -505,8 +505,10 @@ def main():
     __graft_entry__.build()
     res = run_native(args, rank, world)
     if rank == 0 and args.only_step:
+        pm, pn = res["prof"]
         print(json.dumps({"metric": METRIC, "value": res["n_clusters_all"] / (res["ms_step"] * 1e-3),
                           "unit": "clusters/s", "ms_per_step": res["ms_step"], "steps": args.steps,
+                          "stage_ms": {k: v / max(pn, 1) for k, v in pm.items()},
                           "note": "--only-step (profiling run)"}), flush=True)
     elif rank == 0:
         line = finish_native(args, res, world)

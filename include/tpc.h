@@ -211,8 +211,8 @@ int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *in, int32_t 
 
 /* Self-test of the failure path of a bounded device-side wait: a kernel waits on an mbarrier that
  * nothing arrives at, gives up after spin_limit (1..2^20) polls, writes TPC_ERR_TIMEOUT to *status
- * (device int32) and returns; the context stays usable.  The same bounded wait guards the bulk
- * copies of the neighbour-finding kernel.  The paper has no counterpart (diagnostics).
+ * (device int32) and returns; the context stays usable.  The paper has no counterpart
+ * (diagnostics).
  * Errors: INVALID_ARG, CUDA. */
 int tpc_selftest_wait_timeout(int32_t *status, int32_t spin_limit, void *stream);
 

@@ -100,16 +100,22 @@ __device__ int extend(const Work &W, const DevGeom &g, Abg &fy, Abg &fz, int row
     return n;
 }
 
+// Each warp takes 32 x chunk chains at a time from the queue (no CTA barrier: a warp whose chains
+// end early takes the next ones while the others still follow theirs).
 __global__ void __launch_bounds__(128) k_follow(Work W) {
-    __shared__ int s_item;
     const DevGeom &g = *W.geom;
     const int nr = g.n_rows;
+    const int lane = threadIdx.x & 31;
     int n_chains = W.counters[CNT_NCHAINS];
     if (n_chains > W.cap_chains) n_chains = W.cap_chains;
-    const int chunk = blockDim.x * (W.tune.chunk[3] > 0 ? W.tune.chunk[3] : 1);
+    const int chunk = 32 * (W.tune.chunk[3] > 0 ? W.tune.chunk[3] : 1);
     int32_t *q = W.counters + CNT_Q0 + 3;
-    for (int base = queue_next(q, chunk, &s_item); base < n_chains; base = queue_next(q, chunk, &s_item)) {
-        for (int t = base + threadIdx.x; t < base + chunk && t < n_chains; t += blockDim.x) {
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(q, chunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_chains) break;
+        for (int t = base + lane; t < base + chunk && t < n_chains; t += 32) {
             const int start = W.chain_start[t], len = W.chain_len[t], bin = W.chain_bin[t];
             const int row0 = bin % nr;
             const int rowbase = bin - row0;

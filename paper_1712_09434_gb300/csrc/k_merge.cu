@@ -124,8 +124,8 @@ __global__ void k_merge_match(Work W) {
                 const long long XT = e.x;
                 const long long ax = XT - x2;
                 if ((ax < 0 ? -ax : ax) > MERGE_XMAX) continue;
-                const long long yp = y1 + floor_div((XT - x1) * (y2 - y1), dxs);
-                const long long zp = p1.z + floor_div((XT - x1) * (long long)(p2.z - p1.z), dxs);
+                const long long yp = y1 + floor_div_pos((XT - x1) * (y2 - y1), dxs);
+                const long long zp = p1.z + floor_div_pos((XT - x1) * (long long)(p2.z - p1.z), dxs);
                 const long long dy = e.y - yp, dz = e.z - zp;
                 if (dy > W_MERGE || dy < -W_MERGE || dz > W_MERGE || dz < -W_MERGE) continue;
                 const unsigned long long D = (unsigned long long)(dy * dy + dz * dz);

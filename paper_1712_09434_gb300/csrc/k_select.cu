@@ -7,18 +7,21 @@
 //
 // Round: every undecided candidate claims its hits (atomicMax on (round << 32 | ~key), so the
 // latest round wins and inside it the smallest key); an undecided candidate whose hits are all
-// resolved (owned by an accepted candidate = lost, or claimed by itself = kept) decides; one that
-// cannot reach N_MIN even with its unresolved hits is rejected.  Newly accepted candidates then
-// take ownership of their kept hits.  The highest-priority undecided candidate always decides, so
-// the rounds end, and every decision equals the sequential one (a candidate decides only when no
-// higher-priority undecided candidate shares a hit with it).
+// resolved (owned by an accepted candidate = lost, or claimed by itself = kept) decides, and if
+// accepted takes ownership of its kept hits at once; one that cannot reach N_MIN even with its
+// unresolved hits is rejected.  The highest-priority undecided candidate always decides, so the
+// rounds end, and every decision equals the sequential one (a candidate decides only when no
+// higher-priority undecided candidate shares a hit with it).  Two barrier-separated phases per
+// round; each lane loads its row slots first and their owner and claim words together.
 #include "tpc_common.cuh"
 
 namespace tpc {
 
 namespace {
 
-enum { CS_UNDECIDED = 0, CS_ACCEPT_NEW = 1, CS_ACCEPTED = 2, CS_REJECTED = 3 };
+enum { CS_UNDECIDED = 0, CS_ACCEPTED = 2, CS_REJECTED = 3 };
+
+constexpr int SEL_ILP = 5;   // row slots per lane loaded before their dependent loads (5 x 32 >= 159)
 
 __device__ __forceinline__ uint32_t key_of(int n_rows, int n_hits, int local) {
     return ((uint32_t)(n_rows - n_hits) << 23) | (uint32_t)local;
@@ -49,87 +52,105 @@ __global__ void __launch_bounds__(1024) k_select(Work W) {
         for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
             W.cstate[t] = W.cand_n[t] < N_MIN ? CS_REJECTED : CS_UNDECIDED;
         __syncthreads();
+        // Round k: the undecided candidates claim their unowned hits; then each decides.  A
+        // candidate accepted in round k takes ownership of its kept hits at once: only the claimant
+        // of a hit in round k can own it, and a later reader that already sees the owner counts
+        // the hit as lost, which is the sequential answer for it (its owner is accepted).
         int round = 1;
-        for (; round <= SELECT_MAX_ROUNDS; round++) {
-            // claims
+        bool more = true;
+        for (; more && round <= SELECT_MAX_ROUNDS; round++) {
             for (int t = t0 + warp; t < t1; t += nwarps) {
                 if (W.cstate[t] != CS_UNDECIDED) continue;
-                const unsigned long long v =
-                    ((unsigned long long)round << 32) | (uint32_t)~key_of(nr, W.cand_n[t], t - t0);
+                const uint32_t key = key_of(nr, W.cand_n[t], t - t0);
+                const unsigned long long v = ((unsigned long long)round << 32) | (uint32_t)~key;
                 const int rr = W.cand_rows[t];
+                const int ra = rr & 0xffff, rb = rr >> 16;
                 const int32_t *sl = W.cand_slots + (size_t)t * nr;
-                for (int r = (rr & 0xffff) + lane; r <= (rr >> 16); r += 32) {
-                    const int h = sl[r];
-                    if (h >= 0) atomicMax(claim + h, v);
+                for (int r0 = ra; r0 <= rb; r0 += 32 * SEL_ILP) {
+                    int h[SEL_ILP];
+#pragma unroll
+                    for (int j = 0; j < SEL_ILP; j++) {
+                        const int r = r0 + lane + 32 * j;
+                        h[j] = r <= rb ? sl[r] : -1;
+                    }
+#pragma unroll
+                    for (int j = 0; j < SEL_ILP; j++)
+                        if (h[j] >= 0) atomicMax(claim + h[j], v);
                 }
             }
             if (threadIdx.x == 0) s_undecided = 0;
             __syncthreads();
-            // decisions
             for (int t = t0 + warp; t < t1; t += nwarps) {
                 if (W.cstate[t] != CS_UNDECIDED) continue;
                 const uint32_t key = key_of(nr, W.cand_n[t], t - t0);
+                const unsigned long long v = ((unsigned long long)round << 32) | (uint32_t)~key;
                 const int rr = W.cand_rows[t];
+                const int ra = rr & 0xffff, rb = rr >> 16;
                 const int32_t *sl = W.cand_slots + (size_t)t * nr;
                 int sure = 0, unk = 0;
-                for (int r = (rr & 0xffff) + lane; r <= (rr >> 16); r += 32) {
-                    const int h = sl[r];
-                    if (h < 0 || W.owner[h] != KEY_NONE) continue;       // miss, or lost
-                    const unsigned long long v = claim[h];
-                    if ((int)(v >> 32) == round && (uint32_t)~(uint32_t)v == key) sure++; else unk++;
+                int h[SEL_ILP];
+                bool mine[SEL_ILP];
+                for (int r0 = ra; r0 <= rb; r0 += 32 * SEL_ILP) {
+                    unsigned long long cv[SEL_ILP];
+                    uint32_t ov[SEL_ILP];
+#pragma unroll
+                    for (int j = 0; j < SEL_ILP; j++) {
+                        const int r = r0 + lane + 32 * j;
+                        h[j] = r <= rb ? sl[r] : -1;
+                    }
+#pragma unroll
+                    for (int j = 0; j < SEL_ILP; j++)
+                        if (h[j] >= 0) { ov[j] = W.owner[h[j]]; cv[j] = claim[h[j]]; }
+#pragma unroll
+                    for (int j = 0; j < SEL_ILP; j++) {
+                        mine[j] = false;
+                        if (h[j] < 0 || ov[j] != KEY_NONE) continue;       // miss, or lost
+                        if (cv[j] == v) { sure++; mine[j] = true; } else { unk++; }
+                    }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     sure += __shfl_xor_sync(0xffffffffu, sure, o);
                     unk += __shfl_xor_sync(0xffffffffu, unk, o);
                 }
+                if (unk == 0 && sure >= N_MIN) {
+                    if (rb - ra < 32 * SEL_ILP) {      // one pass: this lane's hits are in registers
+#pragma unroll
+                        for (int j = 0; j < SEL_ILP; j++)
+                            if (mine[j]) W.owner[h[j]] = key;
+                    } else {
+                        for (int r = ra + lane; r <= rb; r += 32) {
+                            const int hh = sl[r];
+                            if (hh >= 0 && W.owner[hh] == KEY_NONE && claim[hh] == v) W.owner[hh] = key;
+                        }
+                    }
+                }
                 if (lane == 0) {
-                    if (unk == 0)
-                        W.cstate[t] = sure >= N_MIN ? CS_ACCEPT_NEW : CS_REJECTED;
-                    else if (sure + unk < N_MIN)
+                    if (unk == 0) {
+                        const bool acc = sure >= N_MIN;
+                        W.cstate[t] = acc ? CS_ACCEPTED : CS_REJECTED;
+                        W.seg_n[t] = acc ? sure : 0;
+                    } else if (sure + unk < N_MIN) {
                         W.cstate[t] = CS_REJECTED;
-                    else
+                        W.seg_n[t] = 0;
+                    } else {
                         s_undecided = 1;
+                    }
                 }
             }
             __syncthreads();
-            // ownership of the newly accepted
-            for (int t = t0 + warp; t < t1; t += nwarps) {
-                if (W.cstate[t] != CS_ACCEPT_NEW) continue;
-                const uint32_t key = key_of(nr, W.cand_n[t], t - t0);
-                const unsigned long long v = ((unsigned long long)round << 32) | (uint32_t)~key;
-                const int rr = W.cand_rows[t];
-                const int32_t *sl = W.cand_slots + (size_t)t * nr;
-                for (int r = (rr & 0xffff) + lane; r <= (rr >> 16); r += 32) {
-                    const int h = sl[r];
-                    if (h >= 0 && W.owner[h] == KEY_NONE && claim[h] == v) W.owner[h] = key;
-                }
-                __syncwarp();
-                if (lane == 0) W.cstate[t] = CS_ACCEPTED;
-            }
-            const int undecided = s_undecided;
+            more = s_undecided != 0;
             __syncthreads();
-            if (!undecided) break;
         }
+        round -= 1;
         if (threadIdx.x == 0) {
-            if (round > SELECT_MAX_ROUNDS) set_status(W, ST_TIMEOUT);
+            if (more) set_status(W, ST_TIMEOUT);
             atomicMax(W.counters + CNT_ROUNDS, round);
         }
-        // kept hits per candidate
-        for (int t = t0 + warp; t < t1; t += nwarps) {
-            int kept = 0;
-            if (W.cstate[t] == CS_ACCEPTED) {
-                const uint32_t key = key_of(nr, W.cand_n[t], t - t0);
-                const int rr = W.cand_rows[t];
-                const int32_t *sl = W.cand_slots + (size_t)t * nr;
-                for (int r = (rr & 0xffff) + lane; r <= (rr >> 16); r += 32) {
-                    const int h = sl[r];
-                    kept += h >= 0 && W.owner[h] == key;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-            }
-            if (lane == 0) W.seg_n[t] = kept;
+        // rejected up front, or left undecided by a timeout: no kept hits
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int st = W.cstate[t];
+            if (st == CS_UNDECIDED || (st == CS_REJECTED && W.cand_n[t] < N_MIN)) W.seg_n[t] = 0;
         }
         __syncthreads();
     }

@@ -142,6 +142,21 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {
     return q;
 }
 
+// floor(a / b) for b > 0; operands below 2^24 in magnitude take a float quotient and an exact
+// remainder correction (the quotient of the rounded division is within one of the true floor), the
+// rest the 64-bit integer division.  Same result as floor_div for every input.
+__device__ __forceinline__ long long floor_div_pos(long long a, long long b) {
+    if (a > -(1ll << 24) && a < (1ll << 24) && b < (1ll << 24)) {
+        const int ai = (int)a, bi = (int)b;
+        int q = (int)floorf((float)ai / (float)bi);
+        const int r = ai - q * bi;
+        if (r < 0) q -= 1;
+        else if (r >= bi) q += 1;
+        return q;
+    }
+    return floor_div(a, b);
+}
+
 __device__ __forceinline__ int bin_sector(const DevGeom &g, int bin_in_event) { return bin_in_event / g.n_rows; }
 
 // Work queue: returns the first item of the next chunk for the calling block (thread 0 grabs).
