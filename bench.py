@@ -296,6 +296,8 @@ def run_native(args, rank, world):
     cn = torch.empty(max(n_chains, 1), dtype=torch.int32, device=dev)
     ctx.tpc_debug_copy(5, cn)
     cand_hits = int(cn[:n_chains].sum().item())
+    lens = torch.tensor(np.diff(res["trk_off"]), dtype=torch.float32, device=dev)
+    weighted_hits = int((lens * w_batch[:lens.numel()]).sum().item())
 
     # plain per-event form on the same events
     evs_cl = []
@@ -347,10 +349,24 @@ def run_native(args, rank, world):
                  "tracks_with_reference": int((ref5[:, 0] > 0).sum())}
 
     out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
+               weighted_hits=weighted_hits,
                calib=calib_out,
                n_chains=n_chains, cand_hits=cand_hits)
     ctx.close()
     return out
+
+
+# floating-point operations per hit of the Kalman kernels, counted exactly from csrc/kf.cuh by
+# tests/kf_flop_count.cpp (a fused multiply-add counts two): the gradient kernel runs the forward
+# step twice (forward pass, then the recomputation from the checkpoints) and its adjoint once; the
+# tracking refit runs the square-root forward step
+FLOP_FWD, FLOP_ADJ, FLOP_SQRT_FWD = 507, 933, 434
+# FP32 peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def stage_flops(u):
+    return {"refit": FLOP_SQRT_FWD * u["n_hits"], "refit_grad": (2 * FLOP_FWD + FLOP_ADJ) * u["weighted_hits"]}
 
 
 # algorithmic bytes per stage (compulsory DRAM traffic of each stage's inputs and outputs)
@@ -380,7 +396,17 @@ def finish_native(args, res, world):
     stage_ms = {s: v / k for s, v in prof.items()}
     dom = max(stage_ms, key=lambda s: stage_ms[s])
     byts = stage_bytes(res)
-    achieved = byts[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    flops = stage_flops(res)
+    if dom in flops:       # FP32 arithmetic of the Kalman kernels: the FP32 pipe is the roof
+        achieved = flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "algorithmic_flops": flops[dom]}
+    else:
+        achieved = byts[dom] / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": peak_kind, "algorithmic_bytes": byts[dom]}
     plain_value = res["n_clusters"] / (res["ms_plain"] * 1e-3)
     e2e_value = n_cl_total / (res["ms_e2e"] * 1e-3)
     traffic = None
@@ -408,10 +434,9 @@ def finish_native(args, res, world):
         "tuning": res["tuning"],
         "stage_algorithmic_gbs": {k: byts[k] / (stage_ms[k] * 1e-3) / 1e9 for k in stage_ms if k in byts and stage_ms[k] > 0},
         "units": {"clusters": res["n_clusters"], "chains": res["n_chains"], "candidate_hits": res["cand_hits"],
-                  "tracks": res["n_tracks"], "track_hits": res["n_hits"]},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
-                     "algorithmic_bytes": byts[dom]},
+                  "tracks": res["n_tracks"], "track_hits": res["n_hits"], "weighted_track_hits": res["weighted_hits"]},
+        "roofline": dict(roof, traffic=traffic),
+        "stage_tflops": {k: flops[k] / (stage_ms[k] * 1e-3) / 1e12 for k in flops if stage_ms.get(k, 0) > 0},
         "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
