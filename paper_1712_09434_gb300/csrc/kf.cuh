@@ -107,13 +107,23 @@ KF_HD bool rot_fwd(State<T> &s, T ca, T sa, T kB, T cmin) {
         A[3][j] = s.P[3][j];
         A[4][j] = s.P[4][j];
     }
-    for (int i = 0; i < 5; i++) {
-        s.P[i][0] = j00 * A[i][0];
-        s.P[i][1] = j10 * A[i][0] + A[i][1];
-        s.P[i][2] = j20 * A[i][0] + j22 * A[i][2];
-        s.P[i][3] = A[i][3];
-        s.P[i][4] = A[i][4];
-    }
+    // P' = A J^T, symmetric: the lower triangle, mirrored
+    auto col = [&](int i, int j) -> T {
+        switch (j) {
+            case 0: return j00 * A[i][0];
+            case 1: return j10 * A[i][0] + A[i][1];
+            case 2: return j20 * A[i][0] + j22 * A[i][2];
+            default: return A[i][j];
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            const T v = col(i, j);
+            s.P[i][j] = v;
+            s.P[j][i] = v;
+        }
     s.x = x1;
     s.p[0] = y1;
     s.p[2] = sn1;
@@ -150,16 +160,22 @@ KF_HD void rot_bwd(const State<T> &s, T ca, T sa, T kB, Adj<T> &a) {
     Jb10 *= T(2);
     Jb20 *= T(2);
     Jb22 *= T(2);
-    // G <- J^T G' J
-    for (int j = 0; j < 5; j++) {
-        const T r0 = j00 * GJ[0][j] + j10 * GJ[1][j] + j20 * GJ[2][j];
-        const T r2 = j22 * GJ[2][j];
-        a.G[0][j] = r0;
-        a.G[1][j] = GJ[1][j];
-        a.G[2][j] = r2;
-        a.G[3][j] = GJ[3][j];
-        a.G[4][j] = GJ[4][j];
-    }
+    // G <- J^T G' J (symmetric: the lower triangle, mirrored)
+    auto row = [&](int i, int j) -> T {
+        switch (i) {
+            case 0: return j00 * GJ[0][j] + j10 * GJ[1][j] + j20 * GJ[2][j];
+            case 2: return j22 * GJ[2][j];
+            default: return GJ[i][j];
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            const T v = row(i, j);
+            a.G[i][j] = v;
+            a.G[j][i] = v;
+        }
     // state: x1 = x ca + y sa, y1 = -x sa + y ca, sn1 = sn ca - cs sa, (z, tl, q) unchanged,
     // plus the Jacobian entries' dependence on (sn, tl, q).
     T xb = a.x * ca - a.p[0] * sa;
@@ -241,13 +257,23 @@ KF_HD bool prop_fwd(State<T> &s, T dx, T kB, T smax, T dyref = T(0), T dzref = T
         A[3][j] = s.P[3][j];
         A[4][j] = s.P[4][j];
     }
-    for (int i = 0; i < 5; i++) {
-        s.P[i][0] = A[i][0] + a * A[i][2] + b * A[i][4];
-        s.P[i][1] = A[i][1] + c * A[i][2] + d * A[i][3] + e * A[i][4];
-        s.P[i][2] = A[i][2] + f * A[i][4];
-        s.P[i][3] = A[i][3];
-        s.P[i][4] = A[i][4];
-    }
+    // P' = A F^T, symmetric: the lower triangle, mirrored
+    auto col = [&](int i, int j) -> T {
+        switch (j) {
+            case 0: return A[i][0] + a * A[i][2] + b * A[i][4];
+            case 1: return A[i][1] + c * A[i][2] + d * A[i][3] + e * A[i][4];
+            case 2: return A[i][2] + f * A[i][4];
+            default: return A[i][j];
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            const T v = col(i, j);
+            s.P[i][j] = v;
+            s.P[j][i] = v;
+        }
     s.p[0] += v.dx * v.T_ - dyref;
     s.p[1] += s.p[3] * v.arc - dzref;
     s.p[2] = v.s2;
@@ -282,14 +308,23 @@ KF_HD T prop_bwd(const State<T> &s, T dx, T kB, T smax, Adj<T> &a) {
         F24b += GF[2][k] * s.P[k][4];
     }
     F02b *= T(2); F04b *= T(2); F12b *= T(2); F13b *= T(2); F14b *= T(2); F24b *= T(2);
-    // G <- F^T G' F = F^T GF
-    for (int j = 0; j < 5; j++) {
-        a.G[0][j] = GF[0][j];
-        a.G[1][j] = GF[1][j];
-        a.G[2][j] = GF[2][j] + v.F02 * GF[0][j] + v.F12 * GF[1][j];
-        a.G[3][j] = GF[3][j] + v.F13 * GF[1][j];
-        a.G[4][j] = GF[4][j] + v.F04 * GF[0][j] + v.F14 * GF[1][j] + v.F24 * GF[2][j];
-    }
+    // G <- F^T G' F = F^T GF (symmetric: the lower triangle, mirrored)
+    auto row = [&](int i, int j) -> T {
+        switch (i) {
+            case 2: return GF[2][j] + v.F02 * GF[0][j] + v.F12 * GF[1][j];
+            case 3: return GF[3][j] + v.F13 * GF[1][j];
+            case 4: return GF[4][j] + v.F04 * GF[0][j] + v.F14 * GF[1][j] + v.F24 * GF[2][j];
+            default: return GF[i][j];
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            const T g = row(i, j);
+            a.G[i][j] = g;
+            a.G[j][i] = g;
+        }
 
     // state outputs: y' = y + dx T, z' = z + tl arc, s' = s2, tl' = tl, q' = q, x' = xh
     const T ypb = a.p[0], zpb = a.p[1], spb = a.p[2];
@@ -404,29 +439,26 @@ KF_HD void upd_bwd(const State<T> &s, T ym, T zm, T vy, T vz, Adj<T> &a, T *ymb,
     const T S00 = s.P[0][0] + vy, S01 = s.P[0][1], S11 = s.P[1][1] + vz;
     const T idet = T(1) / (S00 * S11 - S01 * S01);
     const T i00 = S11 * idet, i01 = -S01 * idet, i11 = S00 * idet;
-    T U[5][2], K[5][2];
+    // U = P H^T (columns 0, 1 of P), K = U Si.  With pb the adjoint of p' = p + K r and w = U^T pb:
+    // K^T pb = Si w, and Kb = pb r^T is rank one.
+    T U[5][2];
+    T w0 = T(0), w1 = T(0);
+#pragma unroll
     for (int j = 0; j < 5; j++) {
         U[j][0] = s.P[j][0];
         U[j][1] = s.P[j][1];
-        K[j][0] = U[j][0] * i00 + U[j][1] * i01;
-        K[j][1] = U[j][0] * i01 + U[j][1] * i11;
+        w0 += U[j][0] * a.p[j];
+        w1 += U[j][1] * a.p[j];
     }
-    // rb = K^T pb + 2 Si r
-    T rb0 = T(2) * (i00 * r0 + i01 * r1), rb1 = T(2) * (i01 * r0 + i11 * r1);
-    for (int j = 0; j < 5; j++) {
-        rb0 += K[j][0] * a.p[j];
-        rb1 += K[j][1] * a.p[j];
-    }
-    // Kb = pb r^T
-    T Kb[5][2];
-    for (int j = 0; j < 5; j++) {
-        Kb[j][0] = a.p[j] * r0;
-        Kb[j][1] = a.p[j] * r1;
-    }
+    // rb = K^T pb + 2 Si r = Si (w + 2 r)
+    const T e0 = w0 + T(2) * r0, e1 = w1 + T(2) * r1;
+    const T rb0 = i00 * e0 + i01 * e1, rb1 = i01 * e0 + i11 * e1;
     // GU = G'' U  (5x2)
     T GU[5][2];
+#pragma unroll
     for (int i = 0; i < 5; i++) {
         T g0 = T(0), g1 = T(0);
+#pragma unroll
         for (int k = 0; k < 5; k++) {
             g0 += a.G[i][k] * U[k][0];
             g1 += a.G[i][k] * U[k][1];
@@ -434,30 +466,33 @@ KF_HD void upd_bwd(const State<T> &s, T ym, T zm, T vy, T vz, Adj<T> &a, T *ymb,
         GU[i][0] = g0;
         GU[i][1] = g1;
     }
-    // Sib = r r^T - U^T G'' U + U^T Kb  (then symmetrised)
-    T Sib[2][2];
-    for (int p = 0; p < 2; p++)
-        for (int q = 0; q < 2; q++) {
-            T acc = (p == 0 ? r0 : r1) * (q == 0 ? r0 : r1);
-            for (int k = 0; k < 5; k++) acc += -U[k][p] * GU[k][q] + U[k][p] * Kb[k][q];
-            Sib[p][q] = acc;
-        }
-    const T sb01 = T(0.5) * (Sib[0][1] + Sib[1][0]);
-    Sib[0][1] = sb01;
-    Sib[1][0] = sb01;
-    // Ub = -2 G'' U Si + Kb Si
+    // M = U^T G'' U (symmetric)
+    T M00 = T(0), M01 = T(0), M11 = T(0);
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        M00 += U[k][0] * GU[k][0];
+        M01 += U[k][0] * GU[k][1];
+        M11 += U[k][1] * GU[k][1];
+    }
+    // Sib = r r^T - M + U^T Kb = r r^T - M + w r^T, symmetrised
+    const T sb00 = r0 * r0 - M00 + w0 * r0;
+    const T sb11 = r1 * r1 - M11 + w1 * r1;
+    const T sb01 = r0 * r1 - M01 + T(0.5) * (w0 * r1 + w1 * r0);
+    // Ub = (-2 G'' U + Kb) Si = -2 GU Si + pb (Si r)^T
+    const T q0 = i00 * r0 + i01 * r1, q1 = i01 * r0 + i11 * r1;
     T Ub[5][2];
+#pragma unroll
     for (int j = 0; j < 5; j++) {
-        const T m0 = -T(2) * GU[j][0] + Kb[j][0], m1 = -T(2) * GU[j][1] + Kb[j][1];
-        Ub[j][0] = m0 * i00 + m1 * i01;
-        Ub[j][1] = m0 * i01 + m1 * i11;
+        Ub[j][0] = T(-2) * (GU[j][0] * i00 + GU[j][1] * i01) + a.p[j] * q0;
+        Ub[j][1] = T(-2) * (GU[j][0] * i01 + GU[j][1] * i11) + a.p[j] * q1;
     }
     // Sb = -Si Sib Si
-    T t00 = i00 * Sib[0][0] + i01 * Sib[1][0], t01 = i00 * Sib[0][1] + i01 * Sib[1][1];
-    T t10 = i01 * Sib[0][0] + i11 * Sib[1][0], t11 = i01 * Sib[0][1] + i11 * Sib[1][1];
+    const T t00 = i00 * sb00 + i01 * sb01, t01 = i00 * sb01 + i01 * sb11;
+    const T t10 = i01 * sb00 + i11 * sb01, t11 = i01 * sb01 + i11 * sb11;
     const T Sb00 = -(t00 * i00 + t01 * i01), Sb01 = -(t00 * i01 + t01 * i11);
     const T Sb11 = -(t10 * i01 + t11 * i11);
     // G' = G'' + sym(G_U) + Sb on the (0:2, 0:2) block
+#pragma unroll
     for (int j = 0; j < 5; j++) {
         a.G[j][0] += T(0.5) * Ub[j][0];
         a.G[0][j] += T(0.5) * Ub[j][0];
@@ -624,18 +659,29 @@ KF_HD T upd_fwd_joseph(State<T> &s, T ym, T zm, T vy, T vz) {
     A[0][0] = vy * i00; A[0][1] = vy * i01;
     A[1][0] = vz * i01; A[1][1] = vz * i11;
     for (int j = 2; j < 5; j++) { A[j][0] = -K[j][0]; A[j][1] = -K[j][1]; }
-    // B = A P  (A = [A_c | e_2 e_3 e_4 columns]):  B_ij = A_i0 P_0j + A_i1 P_1j + [i>=2] P_ij
-    T B[5][5];
+    // B = A P (A = [A_c | e_2 e_3 e_4 columns]): B_ij = A_i0 P_0j + A_i1 P_1j + [i>=2] P_ij; the lower
+    // triangle of P_new = B A^T + K R K^T needs columns 0, 1 of B and its lower part from column 2
+    auto B = [&](int i, int j) { return A[i][0] * s.P[0][j] + A[i][1] * s.P[1][j] + (i >= 2 ? s.P[i][j] : T(0)); };
+    T B0[5], B1[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        B0[i] = B(i, 0);
+        B1[i] = B(i, 1);
+    }
+    T Pn[5][5];
+#pragma unroll
     for (int i = 0; i < 5; i++)
-        for (int j = 0; j < 5; j++) B[i][j] = A[i][0] * s.P[0][j] + A[i][1] * s.P[1][j] + (i >= 2 ? s.P[i][j] : T(0));
+#pragma unroll
+        for (int j = 0; j <= i; j++)
+            Pn[i][j] = B0[i] * A[j][0] + B1[i] * A[j][1] + (j >= 2 ? B(i, j) : T(0)) + vy * K[i][0] * K[j][0] +
+                       vz * K[i][1] * K[j][1];
     for (int j = 0; j < 5; j++) s.p[j] += K[j][0] * r0 + K[j][1] * r1;
-    // P_new = B A^T + K R K^T  (lower triangle, mirrored)
+#pragma unroll
     for (int i = 0; i < 5; i++)
+#pragma unroll
         for (int j = 0; j <= i; j++) {
-            const T v = B[i][0] * A[j][0] + B[i][1] * A[j][1] + (j >= 2 ? B[i][j] : T(0)) +
-                        vy * K[i][0] * K[j][0] + vz * K[i][1] * K[j][1];
-            s.P[i][j] = v;
-            s.P[j][i] = v;
+            s.P[i][j] = Pn[i][j];
+            s.P[j][i] = Pn[i][j];
         }
     return chi2;
 }
