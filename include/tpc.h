@@ -17,7 +17,9 @@
  *    errors only.  Errors found on the device (capacity, timeout, bounds) are written to a status
  *    word in the context; tpc_sync_status() waits for the stream and returns it.
  *  - Return codes: TPC_OK (0) or a negative TPC_ERR_* value.  No call aborts or traps.
- *  - A context is not thread-safe: one host thread at a time per context.
+ *  - A context is not thread-safe: one host thread at a time per context.  Its calls share one
+ *    workspace, so they must also be ordered on the device (the same stream, or streams joined
+ *    by events); two calls of one context running concurrently on the device corrupt each other.
  *
  * Coordinates (fixed point; the reading of section 3 used by the integer decisions)
  *  - pad_fp: local y of the cluster in its sector frame in units of lsb_cm (int16).

@@ -44,8 +44,9 @@ __device__ __forceinline__ int lower_y(const int32_t *yz, int lo, int hi, int y)
     return lo;
 }
 
-// Nearest cluster of a row bin to (py, pz) with d^2 <= w^2: row-local index, or -1.
-__device__ int nearest(const Work &W, int bin, int py, int pz, int w) {
+// Nearest cluster of a row bin to (py, pz) with d^2 <= w^2: row-local index, or -1; its packed
+// (Y, Z) goes to *yz (the grid payload, so the cluster arrays need not be read again).
+__device__ int nearest(const Work &W, int bin, int py, int pz, int w, int32_t *yz_out) {
     const int c0 = __ldg(W.bin_off + bin);
     const int32_t *yz = W.gyz + pstart_of(c0, bin);
     const uint16_t *loc = W.gloc + pstart_of(c0, bin);
@@ -54,6 +55,7 @@ __device__ int nearest(const Work &W, int bin, int py, int pz, int w) {
     const long long w2 = (long long)w * w;
     long long bd = w2 + 1;
     int bl = 0x7fffffff;
+    int32_t bv = 0;
     for (int s = zl; s <= zh; s++) {
         const int hi = __ldg(zo + s + 1);
         for (int i = lower_y(yz, __ldg(zo + s), hi, py - w); i < hi; i++) {
@@ -64,9 +66,10 @@ __device__ int nearest(const Work &W, int bin, int py, int pz, int w) {
             const long long d2 = dy * dy + dz * dz;
             if (d2 > w2) continue;
             const int l = __ldg(loc + i);
-            if (d2 < bd || (d2 == bd && l < bl)) { bd = d2; bl = l; }
+            if (d2 < bd || (d2 == bd && l < bl)) { bd = d2; bl = l; bv = v; }
         }
     }
+    *yz_out = bv;
     return bl == 0x7fffffff ? -1 : bl;
 }
 
@@ -83,11 +86,12 @@ __device__ int extend(const Work &W, const DevGeom &g, Abg &fy, Abg &fz, int row
         const long long av = fy.v < 0 ? -fy.v : fy.v;
         if (abs(py) > g.ymax[row] || pz < 0 || pz > g.zmax || av > (long long)V_MAX * 65536) break;
         const int w = W_F0 + W_F1 * misses;
-        const int l = nearest(W, rowbase_bin + row, py, pz, w);
+        int32_t v;
+        const int l = nearest(W, rowbase_bin + row, py, pz, w, &v);
         if (l >= 0) {
             const int h = __ldg(W.bin_off + rowbase_bin + row) + l;
-            abg_update(fy, __ldg(W.pad + h));
-            abg_update(fz, __ldg(W.tim + h));
+            abg_update(fy, (int16_t)(v & 0xffff));
+            abg_update(fz, (int)((uint32_t)v >> 16));
             slots[row] = h;
             *row_end = row;
             n++;

@@ -537,9 +537,19 @@ __global__ void k_len_scatter(Work W, int32_t *hist, int32_t *order) {
     }
 }
 
-// Hit list of caller-provided tracks -> packed (Y, Z, sector, row) per hit; the bin of a cluster is
-// found by binary search in bin_off.
-__global__ void k_pack_hits(Work W) {
+// Bin of every cluster (warp per bin), into a workspace array of N words.
+__global__ void k_cluster_bins(Work W, int32_t *cbin) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int b = gw; b < W.nbins; b += nw) {
+        const int c0 = __ldg(W.bin_off + b), c1 = __ldg(W.bin_off + b + 1);
+        for (int c = max(c0, 0) + lane; c < min(c1, W.n_clusters); c += 32) cbin[c] = b;
+    }
+}
+
+// Hit list of caller-provided tracks -> packed (Y, Z, sector, row) per hit, the bin of each cluster
+// from the map written by k_cluster_bins.
+__global__ void k_pack_hits(Work W, const int32_t *cbin) {
     const int nt = n_tracks_of(W);
     int nh = W.trk_off[nt];
     if (nh > W.cap_hits || nh < 0) {
@@ -555,11 +565,7 @@ __global__ void k_pack_hits(Work W) {
             W.trk_pack[2 * i + 1] = 0;
             continue;
         }
-        int lo = 0, hi = W.nbins;   // last b with bin_off[b] <= h
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (W.bin_off[mid] <= h) lo = mid; else hi = mid;
-        }
+        const int lo = cbin[h];
         const int sector = (lo % nbe) / W.nr, row = lo % W.nr;
         W.trk_pack[2 * i] = (int32_t)((uint32_t)(W.pad[h] & 0xffff) | ((uint32_t)W.tim[h] << 16));
         W.trk_pack[2 * i + 1] = sector | (row << 16);
@@ -568,7 +574,11 @@ __global__ void k_pack_hits(Work W) {
 
 }  // namespace
 
-void launch_pack_hits(const Work &W, cudaStream_t s) { k_pack_hits<<<W.sm_count * 4, 256, 0, s>>>(W); }
+void launch_pack_hits(const Work &W, cudaStream_t s) {
+    // the chain-length scratch of the tracking (one word per cluster) holds the cluster -> bin map
+    k_cluster_bins<<<W.sm_count * 8, 256, 0, s>>>(W, W.clen);
+    k_pack_hits<<<W.sm_count * 4, 256, 0, s>>>(W, W.clen);
+}
 
 int refit_ck_words(int cap_hits, int cap_tracks) { return (cap_hits / CK_K + cap_tracks + 1) * CK_WORDS; }
 int refit_rec_words(int cap_tracks) { return cap_tracks * REC_WORDS; }
