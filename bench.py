@@ -331,6 +331,16 @@ def run_native(args, rank, world):
     th5 = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
     ms_grad, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5, a5, 1), 10, 3)
 
+    # plain per-event tracking of single events: the central event above and a 5,000-track event
+    single = {}
+    ev2 = synth.make_event(synth.full_event())
+    c2 = capi.Clusters.from_numpy(ev2.pad_fp, ev2.time_fp, ev2.bin_off, 1)
+    t2 = capi.Tracks(ev2.n_clusters, 1, ev2.n_clusters // 8 + 1024, ev2.n_clusters)
+    for name, cc, tt, ncl in [("full_event_5000_tracks", c2, t2, ev2.n_clusters),
+                              ("central_20000_tracks", c5, t5, ev5.n_clusters)]:
+        ms_ev, _ = timed(lambda: ctx.tpc_track_event(cc, tt), 10, 3)
+        single[name] = {"clusters": int(ncl), "ms": ms_ev, "clusters_per_s": ncl / (ms_ev * 1e-3)}
+
     # calibration recovery: 20 preconditioned gradient steps from the nominal theta
     from paper_1712_09434_gb300 import calib
     t_cal = time.time()
@@ -350,7 +360,7 @@ def run_native(args, rank, world):
 
     out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
                weighted_hits=weighted_hits,
-               calib=calib_out,
+               calib=calib_out, single=single,
                n_chains=n_chains, cand_hits=cand_hits)
     ctx.close()
     return out
@@ -430,6 +440,7 @@ def finish_native(args, res, world):
                     "event": "central, 20000 tracks, injected calibration, references at the vertex",
                     "tracks": res["n_tracks_c5"]},
         "calibration": res["calib"],
+        "single_event": res["single"],
         "stage_ms": stage_ms,
         "tuning": res["tuning"],
         "stage_algorithmic_gbs": {k: byts[k] / (stage_ms[k] * 1e-3) / 1e9 for k in stage_ms if k in byts and stage_ms[k] > 0},
