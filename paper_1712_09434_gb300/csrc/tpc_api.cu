@@ -27,10 +27,15 @@ struct tpc_ctx {
     int32_t *order, *lhist;   // tracks by decreasing length for the adjoint
     // batch graph cache
     cudaStream_t cap_stream;
-    cudaGraphExec_t gexec;
-    Work gwork;
-    bool gvalid;
-    int gprofile;
+    // a few graphs, keyed by the kernel arguments (e.g. double-buffered inputs), least recently
+    // used replaced first
+    static constexpr int kGraphs = 4;
+    cudaGraphExec_t gexec[kGraphs];
+    Work gwork[kGraphs];
+    bool gvalid[kGraphs];
+    int gprofile[kGraphs];
+    long long gused[kGraphs];
+    long long gclock;
     // per-stage timing (tpc_profile_*): events between the stages of the last call of each kind
     int profile;
     cudaEvent_t ev_pipe[TPC_N_PIPE_STAGES + 1];
@@ -271,10 +276,11 @@ int tpc_reserve(tpc_ctx *c, int32_t max_clusters, int32_t max_events) {
         cudaFree(c->arena);
         c->arena = nullptr;
     }
-    if (c->gvalid) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gvalid = false;
-    }
+    for (int k = 0; k < tpc_ctx::kGraphs; k++)
+        if (c->gvalid[k]) {
+            cudaGraphExecDestroy(c->gexec[k]);
+            c->gvalid[k] = false;
+        }
     c->max_clusters = max_clusters > c->max_clusters ? max_clusters : c->max_clusters;
     c->max_events = max_events > c->max_events ? max_events : c->max_events;
     c->nbins_max = c->max_events * c->hgeom.n_sectors * c->hgeom.n_rows;
@@ -293,7 +299,8 @@ void tpc_destroy(tpc_ctx *c) {
     if (!c) return;
     for (auto &e : c->ev_pipe) if (e) cudaEventDestroy(e);
     for (auto &e : c->ev_refit) if (e) cudaEventDestroy(e);
-    if (c->gvalid) cudaGraphExecDestroy(c->gexec);
+    for (int k = 0; k < tpc_ctx::kGraphs; k++)
+        if (c->gvalid[k]) cudaGraphExecDestroy(c->gexec[k]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->arena) cudaFree(c->arena);
     if (c->dgeom) cudaFree(c->dgeom);
@@ -335,7 +342,16 @@ int tpc_track_batch(tpc_ctx *c, const tpc_clusters *in, tpc_tracks *out, const t
     if ((rc = validate_out(out))) return rc;
     const Work W = make_work(c, in, out, tune);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!c->gvalid || c->gprofile != c->profile || std::memcmp(&W, &c->gwork, sizeof(Work)) != 0) {
+    int slot = -1;
+    for (int k = 0; k < tpc_ctx::kGraphs; k++)
+        if (c->gvalid[k] && c->gprofile[k] == c->profile && std::memcmp(&W, &c->gwork[k], sizeof(Work)) == 0)
+            slot = k;
+    if (slot < 0) {
+        slot = 0;   // an empty slot, else the least recently used
+        for (int k = 0; k < tpc_ctx::kGraphs; k++) {
+            if (!c->gvalid[k]) { slot = k; break; }
+            if (c->gused[k] < c->gused[slot]) slot = k;
+        }
         cudaGraph_t graph = nullptr;
         TPC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         const int erc = enqueue_pipeline(c, W, c->cap_stream, true);
@@ -345,27 +361,28 @@ int tpc_track_batch(tpc_ctx *c, const tpc_clusters *in, tpc_tracks *out, const t
             return erc;
         }
         TPC_CUDA(ce);
-        if (c->gvalid) {
+        if (c->gvalid[slot]) {
             cudaGraphExecUpdateResultInfo info;
-            if (cudaGraphExecUpdate(c->gexec, graph, &info) != cudaSuccess) {
+            if (cudaGraphExecUpdate(c->gexec[slot], graph, &info) != cudaSuccess) {
                 cudaGetLastError();
-                cudaGraphExecDestroy(c->gexec);
-                c->gvalid = false;
+                cudaGraphExecDestroy(c->gexec[slot]);
+                c->gvalid[slot] = false;
             }
         }
-        if (!c->gvalid) {
-            const cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
+        if (!c->gvalid[slot]) {
+            const cudaError_t ie = cudaGraphInstantiate(&c->gexec[slot], graph, 0);
             if (ie != cudaSuccess) {
                 cudaGraphDestroy(graph);
                 return cuda_err(ie);
             }
         }
         cudaGraphDestroy(graph);
-        c->gwork = W;
-        c->gvalid = true;
-        c->gprofile = c->profile;
+        c->gwork[slot] = W;
+        c->gvalid[slot] = true;
+        c->gprofile[slot] = c->profile;
     }
-    TPC_CUDA(cudaGraphLaunch(c->gexec, s));
+    c->gused[slot] = ++c->gclock;
+    TPC_CUDA(cudaGraphLaunch(c->gexec[slot], s));
     if (c->profile) c->pipe_pending = true;
     return TPC_OK;
 }
