@@ -181,8 +181,11 @@ __global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
             for (int j = 0; j < 5; j++) s.S[i][j] = i == j ? SQRT_C0[i] : 0.f;
         float chi2 = 0.f;
         bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
+        HitRaw nxt = n >= 3 ? hit_raw(W, off + n - 1) : HitRaw{};
         for (int i = n - 1; ok && i >= 0; i--) {
-            const HitT m = transform(G, th, ns, hit_raw(W, off + i));
+            const HitRaw cur = nxt;
+            if (i > 0) nxt = hit_raw(W, off + i - 1);      // next hit's load in flight during this step
+            const HitT m = transform(G, th, ns, cur);
             ok = kf::sqrt_step(s, m.f, fg.g, chi2);
         }
         s.p[0] += s.yref;
@@ -348,9 +351,12 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
             for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? C0[i] : 0.f;
         float chi2 = 0.f;
         bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
+        HitRaw nxt = n >= 3 ? hit_raw(W, off + n - 1) : HitRaw{};
         for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q
+            const HitRaw cur = nxt;
+            if (q + 1 < n) nxt = hit_raw(W, off + n - 2 - q);   // next hit's load in flight
             if (GRAD && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
-            const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q), model);
+            const HitT m = transform(G, th, ns, cur, model);
             ok = kf::step_fwd(s, m.f, fg.g, chi2);
         }
         float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
@@ -387,13 +393,18 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
             kf::State<float> st;
             ck_load(ckt + (q0 / CK_K) * CK_WORDS, st);
             float dummy = 0.f;
+            HitRaw nx = hit_raw(W, off + n - 1 - q0);
             for (int q = q0; q < q1; q++) {
+                const HitRaw cur = nx;
+                if (q + 1 < q1) nx = hit_raw(W, off + n - 2 - q);
                 ck_store(buf + (q - q0) * CK_WORDS, st);
-                const HitT m = transform(G, th, ns, hit_raw(W, off + n - 1 - q), model);
+                const HitT m = transform(G, th, ns, cur, model);
                 kf::step_fwd(st, m.f, fg.g, dummy);
             }
+            HitRaw hb = hit_raw(W, off + n - q1);
             for (int q = q1 - 1; q >= q0; q--) {
-                const HitRaw h = hit_raw(W, off + n - 1 - q);
+                const HitRaw h = hb;
+                if (q > q0) hb = hit_raw(W, off + n - q);
                 const HitT m = transform(G, th, ns, h, model);
                 float xb = 0.f, yb = 0.f, zb = 0.f, vyb = 0.f, vzb = 0.f;
                 kf::State<float> sin_;
