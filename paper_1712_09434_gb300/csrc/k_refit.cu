@@ -17,7 +17,7 @@ namespace tpc {
 
 namespace {
 
-constexpr int CK_K = 8;            // steps between checkpoints
+constexpr int CK_K = 16;           // steps between checkpoints
 constexpr int CK_WORDS = 25;       // x, p[5], P lower triangle[15], frame, rref, yref, zref
 constexpr int REC_SEC = 8;         // sector entries per track record
 constexpr int REC_WORDS = 2 + 3 * REC_SEC;
