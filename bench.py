@@ -34,8 +34,8 @@ from paper_1712_09434_gb300 import synth  # noqa: E402
 
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
 # kernels of one step: tracking graph (grid 1, links 1, chains 8, follow 1, select 1, merge 17,
-# refit 1) + refit_grad (cluster bins 1, pack 1, length sort 3, refit_grad 1, reduce 2)
-LAUNCHES_PER_STEP = 38
+# refit 1) + refit_grad (cluster bins 1, pack 1, length sort 3, forward and reverse pass 2, reduce 2)
+LAUNCHES_PER_STEP = 39
 WORKLOAD = "batch-64-events-logU-100-20000-tracks-20pct-noise"
 
 

@@ -314,10 +314,15 @@ __device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
 }
 
 // S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
-template <bool GRAD>
+// MODE 0: forward pass only (objective).  MODE 1: forward pass that also stores the checkpoints and
+// the state after the last hit (frame -1 marks a track whose fit failed).  MODE 2: reverse sweep
+// from those states (the gradient part of the records).  Splitting the forward pass off lets it
+// run with fewer registers and more warps than the adjoint.
+template <int MODE>
 __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta, const float *weight,
                                                     const float *anchor, int model, float *ck, float *rec,
                                                     const int32_t *order) {
+    constexpr bool GRAD = MODE != 0;
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
     const int ns = W.ns, np = 1 + 2 * ns;
@@ -341,39 +346,47 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
         float *r = rec + (size_t)t * REC_WORDS;
         const float w = weight ? weight[t] : 1.f;
         if (w == 0.f) n = 0;   // excluded track: no fit, no adjoint
-        float *ckt = ck + ((size_t)(off / CK_K) + t) * CK_WORDS;
-        kf::State<float> s;
-        s.x = 0.f;
-        s.rref = 0;
-        s.frame = 0;
-        s.yref = s.zref = 0.f;
-        for (int i = 0; i < 5; i++)
-            for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? C0[i] : 0.f;
-        float chi2 = 0.f;
-        bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
-        HitRaw nxt = n >= 3 ? hit_raw(W, off + n - 1) : HitRaw{};
-        for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q
-            const HitRaw cur = nxt;
-            if (q + 1 < n) nxt = hit_raw(W, off + n - 2 - q);   // next hit's load in flight
-            if (GRAD && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
-            const HitT m = transform(G, th, ns, cur, model);
-            ok = kf::step_fwd(s, m.f, fg.g, chi2);
-        }
-        float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
+        // checkpoints of track t: slots [off/CK_K + 2t, ... + ceil(n/CK_K)], the last one the state
+        // after the last hit
+        float *ckt = ck + ((size_t)(off / CK_K) + 2 * (size_t)t) * CK_WORDS;
+        float *ckend = ckt + (size_t)((n + CK_K - 1) / CK_K) * CK_WORDS;
         Anchor A{};
-        const bool use_anchor = anchor != nullptr && ok && (A = load_anchor(anchor, t)).any();
-        for (int j = 0; use_anchor && ok && j < N_ANCHOR_STAGES; j++) {
-            if (GRAD) ck_store(buf + j * CK_WORDS, s);
-            ok = anchor_fwd(s, j, A, fg.g, chi2);
+        bool use_anchor = false;
+        if (MODE != 2) {
+            kf::State<float> s;
+            s.x = 0.f;
+            s.rref = 0;
+            s.frame = 0;
+            s.yref = s.zref = 0.f;
+            for (int i = 0; i < 5; i++)
+                for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? C0[i] : 0.f;
+            float chi2 = 0.f;
+            bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
+            HitRaw nxt = n >= 3 ? hit_raw(W, off + n - 1) : HitRaw{};
+            for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q
+                const HitRaw cur = nxt;
+                if (q + 1 < n) nxt = hit_raw(W, off + n - 2 - q);   // next hit's load in flight
+                if (GRAD && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
+                const HitT m = transform(G, th, ns, cur, model);
+                ok = kf::step_fwd(s, m.f, fg.g, chi2);
+            }
+            if (GRAD && ok) ck_store(ckend, s);
+            use_anchor = anchor != nullptr && ok && (A = load_anchor(anchor, t)).any();
+            for (int j = 0; use_anchor && ok && j < N_ANCHOR_STAGES; j++) ok = anchor_fwd(s, j, A, fg.g, chi2);
+            if (GRAD && n >= 1 && !ok) ckend[21] = __int_as_float(-1);
+            r[0] = ok ? w * chi2 : 0.f;
+            r[1] = 0.f;
+            for (int k = 0; k < REC_SEC; k++) {
+                r[2 + 3 * k] = __int_as_float(-1);
+                r[3 + 3 * k] = 0.f;
+                r[4 + 3 * k] = 0.f;
+            }
+            continue;
         }
-        r[0] = ok ? w * chi2 : 0.f;
-        r[1] = 0.f;
-        for (int k = 0; k < REC_SEC; k++) {
-            r[2 + 3 * k] = __int_as_float(-1);
-            r[3 + 3 * k] = 0.f;
-            r[4 + 3 * k] = 0.f;
-        }
-        if (!GRAD || !ok) continue;
+        // MODE 2: reverse sweep of a track whose forward pass succeeded
+        if (n < 3 || __float_as_int(ckend[21]) < 0) continue;
+        float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
+        use_anchor = anchor != nullptr && (A = load_anchor(anchor, t)).any();
         // reverse sweep, segment by segment from the last checkpoint
         kf::Adj<float> a;
         kf::adj_zero(a);
@@ -381,10 +394,12 @@ __global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta,
         int cur_sec = -1, n_ent = 0;
         float ent_d[REC_SEC], ent_a[REC_SEC];
         int ent_s[REC_SEC];
-        if (use_anchor) {               // the vertex stages first, from the states kept in buf
-            for (int j = N_ANCHOR_STAGES - 1; j >= 0; j--) {
+        if (use_anchor) {               // the vertex stages first, each input recomputed from the
+            for (int j = N_ANCHOR_STAGES - 1; j >= 0; j--) {   // state after the last hit
                 kf::State<float> st;
-                ck_load(buf + j * CK_WORDS, st);
+                ck_load(ckend, st);
+                float dummy = 0.f;
+                for (int jj = 0; jj < j; jj++) anchor_fwd(st, jj, A, fg.g, dummy);
                 anchor_bwd(st, j, A, fg.g, a);
             }
         }
@@ -591,7 +606,7 @@ void launch_pack_hits(const Work &W, cudaStream_t s) {
     k_pack_hits<<<W.sm_count * 4, 256, 0, s>>>(W, W.clen);
 }
 
-int refit_ck_words(int cap_hits, int cap_tracks) { return (cap_hits / CK_K + cap_tracks + 1) * CK_WORDS; }
+int refit_ck_words(int cap_hits, int cap_tracks) { return (cap_hits / CK_K + 2 * cap_tracks + 1) * CK_WORDS; }
 int refit_rec_words(int cap_tracks) { return cap_tracks * REC_WORDS; }
 int refit_part_doubles(int cap_tracks, int ns) { return ((cap_tracks + RED_T - 1) / RED_T + 1) * (2 * ns + 2); }
 
@@ -611,10 +626,13 @@ void launch_refit_grad_fit(const Work &W, const double *theta, const float *weig
     k_len_hist<<<W.sm_count * 4, 256, 0, s>>>(W, hist);
     k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
     k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
-    if (grad)
-        k_refit_grad<true><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
-    else
-        k_refit_grad<false><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+    if (grad) {
+        k_refit_grad<1><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+        cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
+        k_refit_grad<2><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+    } else {
+        k_refit_grad<0><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+    }
 }
 
 void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,
