@@ -14,6 +14,8 @@ constant).  Host logic only: every evaluation runs through the C ABI.
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 
 import numpy as np
 import torch
@@ -124,3 +126,22 @@ def fit_calibration(f, theta0, steps=20, H=None):
     history.append((steps, val, float(np.linalg.norm(g))))
     sigma = np.sqrt(np.maximum(np.diag(2.0 * Hinv), 0.0))
     return CalibResult(theta=theta, history=history, hessian=H, sigma=sigma)
+
+
+def save_theta(path, theta, n_sectors=36, meta=None):
+    """Store a calibration (the calibration objects of the paper's online loop are kept for offline
+    use) as JSON: s_vd, d_k and a_k by name, plus free-form metadata."""
+    th = np.asarray(theta, np.float64)
+    assert th.shape == (1 + 2 * n_sectors,)
+    doc = {"s_vd": float(th[0]), "d": th[1:1 + n_sectors].tolist(), "a": th[1 + n_sectors:].tolist(),
+           "meta": meta or {}}
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(doc, f, indent=1)
+    os.replace(tmp, path)
+
+
+def load_theta(path):
+    """Inverse of save_theta: the float64 theta vector [s_vd, d_0.., a_0..]."""
+    doc = json.load(open(path))
+    return np.concatenate([[doc["s_vd"]], doc["d"], doc["a"]]).astype(np.float64)

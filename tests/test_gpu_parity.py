@@ -290,3 +290,22 @@ def test_launch_shapes_do_not_change_results(ctx):
     with pytest.raises(capi.TpcError) as e:
         ctx.tpc_set_tuning(bad)
     assert e.value.code == capi.TPC_ERR_INVALID_ARG
+
+
+def test_stage_profile_reports_every_stage(ctx):
+    """tpc_profile_*: per-stage CUDA-event times of the tracking graph and of tpc_refit_grad."""
+    from paper_1712_09434_gb300 import capi
+    ev = _events.event("c2")
+    cl = _gpu.clusters_of(ev)
+    ctx.tpc_profile_enable(True)
+    try:
+        ctx.tpc_profile_read(reset=True)
+        g = _gpu.run(ctx, cl, batch=True)
+        _refit_sum_grad(ctx, cl, g["tracks_obj"], synth.theta_nominal(), np.ones(g["n_tracks"]))
+        ms, n_calls = ctx.tpc_profile_read(reset=True)
+    finally:
+        ctx.tpc_profile_enable(False)
+    assert n_calls == 1
+    assert list(ms) == capi.STAGES
+    assert all(v > 0.0 for v in ms.values()), ms
+    assert sum(ms.values()) < 1000.0
