@@ -319,7 +319,7 @@ __device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
 // from those states (the gradient part of the records).  Splitting the forward pass off lets it
 // run with fewer registers and more warps than the adjoint.
 template <int MODE>
-__global__ void __launch_bounds__(128) k_refit_grad(Work W, const double *theta, const float *weight,
+__global__ void __launch_bounds__(128, MODE == 2 ? 4 : 1) k_refit_grad(Work W, const double *theta, const float *weight,
                                                     const float *anchor, int model, float *ck, float *rec,
                                                     const int32_t *order) {
     constexpr bool GRAD = MODE != 0;
