@@ -91,8 +91,10 @@ typedef struct {
 /* Launch shape of the tunable kernels (0 = library default).  Index: 0 grid, 1 links, 2 chains,
  * 3 follow, 4 select, 5 merge, 6 refit, 7 refit_grad.  block = threads per CTA (multiple of 32, at
  * most 256, 128, 256, 128, 1024, 512, 128, 128 by index), ctas_per_sm = CTAs per SM of the grid
- * (<= 64), chunk = work items taken per queue grab (<= 64; used by the following).  Launch shapes
- * never change results. */
+ * (<= 64), chunk = work items taken per queue grab (<= 64; used by the following); for the neighbour
+ * finding (index 1) chunk = 1 selects the variant that stages rows r+-1 of every bin in shared
+ * memory by bulk copies (one CTA per bin) instead of reading them through L1 (one warp per bin).
+ * Launch shapes never change results. */
 typedef struct {
     int32_t block[TPC_N_TUNE];
     int32_t ctas_per_sm[TPC_N_TUNE];

@@ -21,6 +21,7 @@ namespace tpc {
 namespace {
 
 constexpr int LINK_BLOCK = 128;         // threads per CTA of the neighbour finding (at most)
+constexpr int LINK_STAGE_CAP = 2048;    // clusters of one row staged in shared memory (staged kernel)
 constexpr int LINK_DCAP = 12;           // down-row candidates of a window kept in shared memory
 
 __device__ __forceinline__ int warp_incl(int v) {
@@ -92,13 +93,24 @@ __global__ void __launch_bounds__(256) k_grid(Work W) {
     }
 }
 
-// ---- mbarrier with a bounded wait (used by the failure-path self-test) --------------------------
+// ---- bulk copy (global -> shared) on an mbarrier, with a bounded wait --------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = SPIN_LIMIT) {
     for (long long it = 0; it < limit; ++it) {
@@ -230,6 +242,151 @@ __global__ void __launch_bounds__(LINK_BLOCK) k_links(Work W) {
     }
 }
 
+// The same search with rows r-1 and r+1 of every bin staged in shared memory by bulk copies
+// (cp.async.bulk on an mbarrier, bounded wait), one CTA per bin, down candidates in registers.
+// Selected by tuning (chunk of kernel 1 = 1); measured slower than the L1 version on GB300 (the
+// per-bin copy and the CTA barriers cost more than the reuse saves), kept for the autotuner.
+__global__ void __launch_bounds__(128) k_links_staged(Work W) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    int32_t *s_yz[2] = {(int32_t *)smem, (int32_t *)(smem + LINK_STAGE_CAP * 4)};
+    uint16_t *s_loc[2] = {(uint16_t *)(smem + 2 * LINK_STAGE_CAP * 4),
+                          (uint16_t *)(smem + 2 * LINK_STAGE_CAP * 4 + LINK_STAGE_CAP * 2)};
+    __shared__ uint16_t s_zo[2][ZOFF_STRIDE + 1];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item;
+    const DevGeom &g = *W.geom;
+    const int nbe = g.n_sectors * g.n_rows;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    int32_t *q = W.counters + CNT_Q0 + 1;
+    for (int b = queue_next(q, 1, &s_item); b < W.nbins; b = queue_next(q, 1, &s_item)) {
+        const int r = (b % nbe) % g.n_rows;
+        const int c0 = W.bin_off[b], c1 = W.bin_off[b + 1];
+        if (r == 0 || r == g.n_rows - 1) {
+            for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) { W.up[c] = -1; W.down[c] = -1; }
+            continue;
+        }
+        RowView rv[2];
+        int nb[2], cb[2];
+        bool staged_any = false;
+        uint32_t tx = 0;
+        for (int k = 0; k < 2; k++) {
+            const int bb = k == 0 ? b - 1 : b + 1;          // 0: down row, 1: up row
+            cb[k] = W.bin_off[bb];
+            nb[k] = W.bin_off[bb + 1] - cb[k];
+            const int ps = pstart_of(cb[k], bb);
+            for (int i = threadIdx.x; i <= NZB; i += blockDim.x) s_zo[k][i] = W.zoff[(size_t)bb * ZOFF_STRIDE + i];
+            rv[k].zo = s_zo[k];
+            if (nb[k] > 0 && nb[k] <= LINK_STAGE_CAP) {
+                rv[k].yz = s_yz[k];
+                rv[k].loc = s_loc[k];
+                staged_any = true;
+                tx += ((nb[k] * 4 + 15) & ~15) + ((nb[k] * 2 + 15) & ~15);
+            } else {
+                rv[k].yz = W.gyz + ps;
+                rv[k].loc = W.gloc + ps;
+            }
+        }
+        if (staged_any && threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar, tx);
+            for (int k = 0; k < 2; k++) {
+                if (nb[k] > 0 && nb[k] <= LINK_STAGE_CAP) {
+                    const int bb = k == 0 ? b - 1 : b + 1;
+                    const int ps = pstart_of(cb[k], bb);
+                    bulk_g2s(s_yz[k], W.gyz + ps, (nb[k] * 4 + 15) & ~15, &bar);
+                    bulk_g2s(s_loc[k], W.gloc + ps, (nb[k] * 2 + 15) & ~15, &bar);
+                }
+            }
+        }
+        __syncthreads();
+        if (staged_any) {
+            const bool ok = mbar_wait(&bar, phase);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) set_status(W, ST_TIMEOUT);
+                mbar_wait(&bar, phase);   // give the copies in flight a second bounded chance
+                return;
+            }
+            phase ^= 1u;
+        }
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            const int yc = W.pad[c], zc = W.tim[c];
+            const int zl = slab_of(max(zc - W_LINK, 0)), zh = slab_of(zc + W_LINK);
+            // down-row candidates inside the window, kept in registers (a window holds a few;
+            // more than DCAP falls back to rescanning the down row for every up candidate)
+            constexpr int DCAP = 8;
+            int dyv[DCAP], dzv[DCAP], dlv[DCAP];
+            int nd = 0;
+            for (int sd = zl; sd <= zh; sd++) {
+                const int hd = rv[0].zo[sd + 1];
+                for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
+                    const int32_t vd = rv[0].yz[id];
+                    const int yd = (int16_t)(vd & 0xffff);
+                    if (yd > yc + W_LINK) break;
+                    const int zd = (int)((uint32_t)vd >> 16);
+                    if (abs(zd - zc) > W_LINK) continue;
+                    if (nd < DCAP) {
+#pragma unroll
+                        for (int k = 0; k < DCAP; k++)
+                            if (k == nd) { dyv[k] = yd; dzv[k] = zd; dlv[k] = rv[0].loc[id]; }
+                    }
+                    nd++;
+                }
+            }
+            unsigned long long best = ~0ull;
+            if (nd > 0) {
+                for (int su = zl; su <= zh; su++) {
+                    const int hi = rv[1].zo[su + 1];
+                    for (int iu = lower_y(rv[1].yz, rv[1].zo[su], hi, yc - W_LINK); iu < hi; iu++) {
+                        const int32_t vu = rv[1].yz[iu];
+                        const int yu = (int16_t)(vu & 0xffff);
+                        if (yu > yc + W_LINK) break;
+                        const int zu = (int)((uint32_t)vu >> 16);
+                        if (abs(zu - zc) > W_LINK) continue;
+                        const unsigned long long lu = (unsigned long long)rv[1].loc[iu] << 16;
+                        if (nd <= DCAP) {
+#pragma unroll
+                            for (int k = 0; k < DCAP; k++) {
+                                if (k < nd) {
+                                    const long long ey = yu + dyv[k] - 2 * yc, ez = zu + dzv[k] - 2 * zc;
+                                    const long long D = ey * ey + ez * ez;
+                                    const unsigned long long key = ((unsigned long long)D << 32) | lu | dlv[k];
+                                    if (D <= D_MAX && key < best) best = key;
+                                }
+                            }
+                        } else {
+                            for (int sd = zl; sd <= zh; sd++) {
+                                const int hd = rv[0].zo[sd + 1];
+                                for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
+                                    const int32_t vd = rv[0].yz[id];
+                                    const int yd = (int16_t)(vd & 0xffff);
+                                    if (yd > yc + W_LINK) break;
+                                    const int zd = (int)((uint32_t)vd >> 16);
+                                    if (abs(zd - zc) > W_LINK) continue;
+                                    const long long ey = yu + yd - 2 * yc, ez = zu + zd - 2 * zc;
+                                    const long long D = ey * ey + ez * ez;
+                                    if (D > D_MAX) continue;
+                                    const unsigned long long key = ((unsigned long long)D << 32) | lu | rv[0].loc[id];
+                                    best = key < best ? key : best;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (best != ~0ull) {
+                W.up[c] = cb[1] + (int)((best >> 16) & 0xffff);
+                W.down[c] = cb[0] + (int)(best & 0xffff);
+            } else {
+                W.up[c] = -1;
+                W.down[c] = -1;
+            }
+        }
+        __syncthreads();   // shared rows are overwritten by the next bin's copies
+    }
+}
+
 }  // namespace
 
 void launch_grid(const Work &W, cudaStream_t s) {
@@ -241,9 +398,18 @@ void launch_grid(const Work &W, cudaStream_t s) {
     k_grid<<<grid, block, 0, s>>>(W);
 }
 
-void prepare_kernels() {}
+void prepare_kernels() {
+    cudaFuncSetAttribute(k_links_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, LINK_STAGE_CAP * 12);
+}
 
 void launch_links(const Work &W, cudaStream_t s) {
+    if (W.tune.chunk[1] == 1) {     // rows staged in shared memory, CTA per bin
+        const int block = W.tune.block[1] > 0 ? W.tune.block[1] : 128;
+        int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 8;
+        if (grid > W.nbins) grid = W.nbins > 0 ? W.nbins : 1;
+        k_links_staged<<<grid, block, (size_t)LINK_STAGE_CAP * 12, s>>>(W);
+        return;
+    }
     const int block = W.tune.block[1] > 0 ? W.tune.block[1] : 128;
     int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 16;
     const int warps = block / 32;

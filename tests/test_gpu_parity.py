@@ -277,15 +277,17 @@ def test_launch_shapes_do_not_change_results(ctx):
     g0, s0, gr0 = run_all()
     shapes = {"grid": (64, 8, 0), "links": (64, 4, 0), "chains": (128, 8, 0), "follow": (64, 4, 2),
               "select": (256, 1, 0), "merge": (512, 4, 0), "refit": (64, 2, 0), "refit_grad": (64, 2, 0)}
-    ctx.tpc_set_tuning(tune.to_struct(shapes))
-    try:
-        g1, s1, gr1 = run_all()
-    finally:
-        ctx.tpc_set_tuning(None)
-    for k in ("trk_off", "trk_hits", "label", "par", "cov", "chi2", "ndf"):
-        np.testing.assert_array_equal(g0[k], g1[k], err_msg=k)
-    assert s0 == s1
-    np.testing.assert_array_equal(gr0, gr1)
+    staged = dict(shapes, links=(128, 8, 1))        # neighbour rows staged in shared memory
+    for sh in (shapes, staged):
+        ctx.tpc_set_tuning(tune.to_struct(sh))
+        try:
+            g1, s1, gr1 = run_all()
+        finally:
+            ctx.tpc_set_tuning(None)
+        for k in ("trk_off", "trk_hits", "label", "par", "cov", "chi2", "ndf"):
+            np.testing.assert_array_equal(g0[k], g1[k], err_msg=k)
+        assert s0 == s1
+        np.testing.assert_array_equal(gr0, gr1)
     bad = tune.to_struct({"links": (256, 4, 0)})            # above the kernel's 128 threads
     with pytest.raises(capi.TpcError) as e:
         ctx.tpc_set_tuning(bad)
