@@ -160,6 +160,59 @@ def track_event(pad, tim, bin_off, g=None, keep_stages=False):
     return out
 
 
+def frame_merge(pad, tim, bin_off, n_slices, slice_len, trk_off, trk_hits, ev_trk_off, g=None):
+    """S11 slice merge of a time frame: links next[track] (slice j+1 -> slice j) or -1."""
+    nt = int(trk_off.shape[0]) - 1
+    nxt = np.empty(max(nt, 1), np.int32)
+    rc = lib().or_frame_merge(_geom(g), _p(np.ascontiguousarray(pad, np.int16)),
+                              _p(np.ascontiguousarray(tim, np.uint16)), _p(np.ascontiguousarray(bin_off, np.int32)),
+                              ctypes.c_int32(pad.shape[0]), ctypes.c_int32(n_slices), ctypes.c_int32(slice_len),
+                              ctypes.c_int32(nt), _p(np.ascontiguousarray(trk_off, np.int32)),
+                              _p(np.ascontiguousarray(trk_hits, np.int32)),
+                              _p(np.ascontiguousarray(ev_trk_off, np.int32)), _p(nxt))
+    assert rc == 0, rc
+    return nxt[:nt]
+
+
+def frame_assemble(n_clusters, trk_off, trk_hits, nxt):
+    """Frame tracks from the slice tracks and their links: (ftrk_off, ftrk_hits, flabel)."""
+    nt = int(trk_off.shape[0]) - 1
+    off = np.zeros(nt + 2, np.int32)
+    hits = np.empty(max(int(trk_hits.shape[0]), 1), np.int32)
+    label = np.empty(max(n_clusters, 1), np.int32)
+    nf = lib().or_frame_assemble(ctypes.c_int32(n_clusters), ctypes.c_int32(nt),
+                                 _p(np.ascontiguousarray(trk_off, np.int32)),
+                                 _p(np.ascontiguousarray(trk_hits, np.int32)), _p(np.ascontiguousarray(nxt, np.int32)),
+                                 _p(off), _p(hits), _p(label), ctypes.c_int32(nt + 1), ctypes.c_int32(hits.shape[0]))
+    assert nf >= 0, nf
+    return off[:nf + 1].copy(), hits[:off[nf]].copy(), label[:n_clusters].copy()
+
+
+def track_frame(pad, tim, bin_off, n_slices, slice_len, g=None):
+    """A time frame: S2-S7 on every slice (as one event each, tracks concatenated in slice order
+    with global cluster indices), then the S11 slice merge and the frame tracks."""
+    gg = g if g is not None else geometry()
+    nbe = gg.n_sectors * gg.n_rows
+    bin_off = np.ascontiguousarray(bin_off, np.int64)
+    offs, hits, ev_trk_off = [np.zeros(1, np.int64)], [], [0]
+    for j in range(n_slices):
+        a, b = int(bin_off[j * nbe]), int(bin_off[(j + 1) * nbe])
+        o = track_event(pad[a:b], tim[a:b], (bin_off[j * nbe:(j + 1) * nbe + 1] - a).astype(np.int32), g)
+        offs.append(o["trk_off"][1:].astype(np.int64) + (offs[-1][-1] if len(offs[-1]) else 0))
+        hits.append(o["trk_hits"].astype(np.int64) + a)
+        ev_trk_off.append(ev_trk_off[-1] + len(o["trk_off"]) - 1)
+    trk_off = np.concatenate(offs).astype(np.int32)
+    trk_hits = np.concatenate(hits).astype(np.int32) if hits else np.zeros(0, np.int32)
+    ev_trk_off = np.array(ev_trk_off, np.int32)
+    n = int(pad.shape[0])
+    label = -np.ones(n, np.int32)
+    label[trk_hits] = np.repeat(np.arange(len(trk_off) - 1, dtype=np.int32), np.diff(trk_off))
+    nxt = frame_merge(pad, tim, bin_off.astype(np.int32), n_slices, slice_len, trk_off, trk_hits, ev_trk_off, g)
+    foff, fhits, flabel = frame_assemble(n, trk_off, trk_hits, nxt)
+    return dict(trk_off=trk_off, trk_hits=trk_hits, ev_trk_off=ev_trk_off, label=label, next=nxt,
+                ftrk_off=foff, ftrk_hits=fhits, flabel=flabel)
+
+
 def fit(pad, tim, bin_off, trk_off, trk_hits, theta=None, g=None):
     """S8 FP64 Kalman refit: dict(par [T,5], xref [T], cov [T,15], chi2 [T], ndf [T])."""
     gg = g if g is not None else geometry()

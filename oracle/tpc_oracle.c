@@ -15,8 +15,10 @@
  *
  * Parity status: links (brute force), selection (naive greedy), the partition invariant, the fit
  * (noise-free helices, chi2 statistics, least-squares optimum) and the gradient (central
- * differences of this file's own objective) are pinned by the CPU tests.  Track-finding
- * efficiency on these synthetic events has no printed value in the paper: parity unpinned.
+ * differences of this file's own objective) are pinned by the CPU tests; the time-frame slice
+ * merge by a constructed track cut by a slice boundary, the single-slice and whole-slice-delay
+ * invariances and the truth of its links.  Track-finding efficiency on these synthetic events
+ * has no printed value in the paper: parity unpinned.
  */
 #define _USE_MATH_DEFINES
 #include <math.h>
@@ -439,6 +441,115 @@ int32_t or_assemble(int32_t n, int32_t n_rows, int32_t n_seg, const int32_t *seg
     }
 done:
     free(next); free(prev); free(seen);
+    return nt;
+}
+
+/* S11  Time-frame slice merge (section 3, its outlook for continuous readout: a time frame is cut
+ * along the drift-time axis, the slices are tracked one by one, and the track segments are merged
+ * afterwards).  The clusters are those of n_slices consecutive slices of slice_len LSB of readout
+ * time, with slice-local times, in the layout of a batch of events (bin = (slice, sector, row));
+ * the tracks are the per-slice tracking output in slice order (ev_trk_off[j] = first track of
+ * slice j), hits in track order.
+ *
+ * A track keeps a readout time that falls outwards (drift length shrinks as |z| grows), so the
+ * piece of a track in slice j+1 (S) ends, at its outer end, where the piece in slice j (T)
+ * begins.  The outer end of S (its last hit and the hit MERGE_BACK positions earlier, on integer
+ * (Xtab[row], Y, Z)), with the times moved into slice j by + slice_len, is extrapolated linearly
+ * (floor division) to the row of T's first hit and compared there with the merge windows.  T's
+ * first hit lies in the sector of S's last hit, or in an adjacent sector of the same side; then
+ * the end of S is first rotated into T's frame exactly as in the inter-sector merge.  Mutual best
+ * pairs (smallest (D, index) on both sides) are linked S -> T. */
+static int frame_match(const or_geom *g, const int16_t *pad, const uint16_t *tim, const int32_t *bins,
+                       int32_t slice_len, const int32_t *hs, int ns, int32_t hT, int64_t *D_out) {
+    const int nbe = g->n_sectors * g->n_rows, half = g->n_sectors / 2;
+    int32_t hL = hs[ns - 1], hB = hs[ns - 1 - OR_MERGE_BACK];
+    int ks = (bins[hL] % nbe) / g->n_rows, kt = (bins[hT] % nbe) / g->n_rows;
+    int sgn;
+    if ((ks < half) != (kt < half)) return 0;
+    if (ks == kt) sgn = 0;                                        /* same sector            */
+    else if ((ks % half + 1) % half == kt % half) sgn = +1;       /* T in the next sector   */
+    else if ((kt % half + 1) % half == ks % half) sgn = -1;       /* T in the previous one  */
+    else return 0;
+    int64_t X2 = g->xtab[bins[hL] % g->n_rows], Y2 = pad[hL], Z2 = (int64_t)tim[hL] + slice_len;
+    int64_t X1 = g->xtab[bins[hB] % g->n_rows], Y1 = pad[hB], Z1 = (int64_t)tim[hB] + slice_len;
+    int64_t x1 = X1, y1 = Y1, x2 = X2, y2 = Y2;
+    if (sgn != 0) {
+        x2 = floor_shift(X2 * g->c30 + sgn * Y2 * g->s30, 30);
+        y2 = floor_shift(-sgn * X2 * g->s30 + Y2 * g->c30, 30);
+        x1 = floor_shift(X1 * g->c30 + sgn * Y1 * g->s30, 30);
+        y1 = floor_shift(-sgn * X1 * g->s30 + Y1 * g->c30, 30);
+    }
+    int64_t XT = g->xtab[bins[hT] % g->n_rows], YT = pad[hT], ZT = tim[hT];
+    int64_t dxs = x2 - x1;
+    if (dxs <= 0) return 0;
+    if (iabs64(XT - x2) > OR_MERGE_XMAX) return 0;
+    int64_t yp = y1 + floor_div((XT - x1) * (y2 - y1), dxs);
+    int64_t zp = Z1 + floor_div((XT - x1) * (Z2 - Z1), dxs);
+    int64_t dy = YT - yp, dz = ZT - zp;
+    if (iabs64(dy) > OR_W_MERGE || iabs64(dz) > OR_W_MERGE) return 0;
+    *D_out = dy * dy + dz * dz;
+    return 1;
+}
+
+int or_frame_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
+                   int32_t n, int32_t n_slices, int32_t slice_len, int32_t n_trk, const int32_t *trk_off,
+                   const int32_t *trk_hits, const int32_t *ev_trk_off, int32_t *next) {
+    or_geom g;
+    if (make_geom(gin, &g)) return -1;
+    if (n_slices < 1 || slice_len < 1) return -1;
+    int32_t *bins = cluster_bins(bin_off, n_slices * g.n_sectors * g.n_rows, n);
+    int64_t *bestT_D = (int64_t *)malloc(sizeof(int64_t) * (n_trk + 1));
+    int32_t *bestT = (int32_t *)malloc(sizeof(int32_t) * (n_trk + 1));
+    int64_t *bestS_D = (int64_t *)malloc(sizeof(int64_t) * (n_trk + 1));
+    int32_t *bestS = (int32_t *)malloc(sizeof(int32_t) * (n_trk + 1));
+    for (int32_t i = 0; i < n_trk; i++) { bestT[i] = -1; bestS[i] = -1; next[i] = -1; }
+    for (int j = 0; j + 1 < n_slices; j++) {
+        for (int32_t s = ev_trk_off[j + 1]; s < ev_trk_off[j + 2]; s++) {
+            int ns = trk_off[s + 1] - trk_off[s];
+            if (ns <= OR_MERGE_BACK) continue;
+            const int32_t *hs = trk_hits + trk_off[s];
+            for (int32_t t = ev_trk_off[j]; t < ev_trk_off[j + 1]; t++) {
+                int64_t D;
+                if (trk_off[t + 1] <= trk_off[t]) continue;
+                if (!frame_match(&g, pad, tim, bins, slice_len, hs, ns, trk_hits[trk_off[t]], &D)) continue;
+                if (bestT[s] < 0 || D < bestT_D[s] || (D == bestT_D[s] && t < bestT[s])) { bestT[s] = t; bestT_D[s] = D; }
+                if (bestS[t] < 0 || D < bestS_D[t] || (D == bestS_D[t] && s < bestS[t])) { bestS[t] = s; bestS_D[t] = D; }
+            }
+        }
+    }
+    for (int32_t s = 0; s < n_trk; s++)
+        if (bestT[s] >= 0 && bestS[bestT[s]] == s) next[s] = bestT[s];
+    free(bestT_D); free(bestT); free(bestS_D); free(bestS); free(bins);
+    return 0;
+}
+
+/* Frame tracks: one per chain of linked slice tracks, ordered by the index of the chain's first
+ * track; hits in chain order (links only go from slice j+1 to slice j, so there is no cycle).
+ * Writes ftrk_off (n_ftrk+1), ftrk_hits and flabel (frame track id or -1).  Returns n_ftrk, or -2
+ * when a capacity is exceeded. */
+int32_t or_frame_assemble(int32_t n, int32_t n_trk, const int32_t *trk_off, const int32_t *trk_hits,
+                          const int32_t *next, int32_t *ftrk_off, int32_t *ftrk_hits, int32_t *flabel,
+                          int32_t cap_trk, int32_t cap_hits) {
+    char *has_prev = (char *)calloc(n_trk + 1, 1);
+    for (int32_t i = 0; i < n_trk; i++) if (next[i] >= 0) has_prev[next[i]] = 1;
+    for (int32_t c = 0; c < n; c++) flabel[c] = -1;
+    int32_t nt = 0, nh = 0;
+    ftrk_off[0] = 0;
+    for (int32_t i = 0; i < n_trk; i++) {
+        if (has_prev[i]) continue;
+        if (nt >= cap_trk) { nt = -2; break; }
+        for (int32_t x = i; x >= 0; x = next[x]) {
+            for (int32_t k = trk_off[x]; k < trk_off[x + 1]; k++) {
+                if (nh >= cap_hits) { nt = -2; goto done; }
+                ftrk_hits[nh++] = trk_hits[k];
+                flabel[trk_hits[k]] = nt;
+            }
+        }
+        nt++;
+        ftrk_off[nt] = nh;
+    }
+done:
+    free(has_prev);
     return nt;
 }
 

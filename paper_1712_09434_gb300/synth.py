@@ -426,3 +426,71 @@ def concat_events(events) -> Batch:
                  time_fp=np.concatenate([e.time_fp for e in events]),
                  charge=np.concatenate([e.charge for e in events]),
                  bin_off=bin_off.astype(np.int32), ev_off=ev_off, events=list(events))
+
+
+# ---- continuous readout: time frames sliced along the drift-time axis -------------------------
+
+DRIFT_LSB = 32000          # one full drift length in LSB (250 cm / LSB)
+
+
+@dataclasses.dataclass
+class TimeFrame:
+    """Collisions overlaid in one continuous readout stream and cut into slices of slice_len LSB
+    of readout time.  Readout time of a cluster = t0 of its collision + its drift length (both in
+    LSB of drift length).  Slice j holds the clusters with j*slice_len <= time < (j+1)*slice_len,
+    with time_fp = time - j*slice_len; inside a slice the clusters are sorted by (sector, row, pad,
+    time_fp, collision, index in the collision), and the slices are concatenated in order."""
+    pad_fp: np.ndarray        # int16  [N]
+    time_fp: np.ndarray       # uint16 [N] slice-local readout time
+    bin_off: np.ndarray       # int32  [n_slices*36*159+1] global cluster offsets per (slice, sector, row)
+    ev_off: np.ndarray        # int64  [n_slices+1] cluster offsets per slice
+    slice_len: int
+    t0: np.ndarray            # int64  [K] collision times
+    mc: np.ndarray            # int64  [N] collision << 32 | generating track, or -1 (noise)
+    collisions: list
+
+    @property
+    def n_slices(self):
+        return int(self.ev_off.shape[0] - 1)
+
+    @property
+    def n_clusters(self):
+        return int(self.pad_fp.shape[0])
+
+
+def time_frame(events, per_drift=5.0, slice_len=DRIFT_LSB, seed=3000, t0=None) -> TimeFrame:
+    """Overlay the events at collision times of a Poisson process with per_drift collisions per
+    drift length on average (the first at time 0), or at the given times t0, and slice the
+    stream."""
+    if not 1 <= slice_len <= Z_MAX_LSB + 1:      # slice-local times stay inside [0, Z_MAX_LSB]
+        raise ValueError("slice_len must lie in [1, %d]" % (Z_MAX_LSB + 1))
+    K = len(events)
+    if t0 is None:
+        rng = np.random.default_rng(seed)
+        gaps = rng.exponential(DRIFT_LSB / per_drift, size=K)
+        gaps[0] = 0.0
+        t0 = np.floor(np.cumsum(gaps)).astype(np.int64)
+    t0 = np.asarray(t0, np.int64)
+    if t0.shape != (K,) or (K and t0.min() < 0):
+        raise ValueError("t0 must hold one non-negative time per event")
+    nb = N_SECTORS * N_ROWS
+    parts = []
+    for k, e in enumerate(events):
+        n = e.n_clusters
+        b = np.repeat(np.arange(nb), np.diff(e.bin_off[:nb + 1].astype(np.int64)))
+        tau = t0[k] + e.time_fp.astype(np.int64)
+        mc = np.where(e.mc_track >= 0, (np.int64(k) << 32) | e.mc_track.astype(np.int64), -1)
+        parts.append((b, e.pad_fp.astype(np.int64), tau, np.full(n, k, np.int64), np.arange(n, dtype=np.int64), mc))
+    b, pad, tau, col, idx, mc = (np.concatenate([p[i] for p in parts]) for i in range(6))
+    sl = tau // slice_len
+    loc = tau - sl * slice_len
+    n_sl = int(sl.max()) + 1 if sl.size else 1
+    gbin = sl * nb + b
+    o = np.lexsort((idx, col, loc, pad, gbin))
+    gbin, pad, loc, mc = gbin[o], pad[o], loc[o], mc[o]
+    bin_off = np.searchsorted(gbin, np.arange(n_sl * nb + 1), side="left")
+    if bin_off[-1] >= 2**31:
+        raise ValueError("time frame exceeds 2^31 clusters")
+    ev_off = bin_off[::nb].astype(np.int64)
+    return TimeFrame(pad_fp=pad.astype(np.int16), time_fp=loc.astype(np.uint16), bin_off=bin_off.astype(np.int32),
+                     ev_off=ev_off, slice_len=int(slice_len), t0=t0, mc=mc, collisions=list(events))
