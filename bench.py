@@ -24,6 +24,7 @@ import sys
 import tempfile
 import threading
 import time
+import types
 
 import numpy as np
 
@@ -62,6 +63,31 @@ def make_batch(n_events, seed0):
     os.replace(tmp, cache)
     log("generated %d events, %d clusters in %.1f s" % (n_events, b.n_clusters, time.time() - t))
     return d
+
+
+def make_frame(n_events, seed0, per_drift=5.0, slice_len=synth.DRIFT_LSB, seed=3000):
+    """The events of the batch overlaid in one continuous readout stream (collision times of a
+    Poisson process, per_drift collisions per drift length) and cut into slices of slice_len LSB."""
+    cache = os.path.join(tempfile.gettempdir(), "tpc_frame_%d_%d_%g_%d_%d.npz" % (n_events, seed0, per_drift,
+                                                                                   slice_len, seed))
+    if os.path.exists(cache):
+        return dict(np.load(cache, allow_pickle=False))
+    d = make_batch(n_events, seed0)
+    t = time.time()
+    evs = []
+    for e in range(n_events):
+        a, b = int(d["ev_off"][e]), int(d["ev_off"][e + 1])
+        evs.append(types.SimpleNamespace(pad_fp=d["pad"][a:b], time_fp=d["tim"][a:b], bin_off=d["ev_bin_off"][e],
+                                         mc_track=np.full(b - a, -1, np.int32), n_clusters=b - a))
+    tf = synth.time_frame(evs, per_drift=per_drift, slice_len=slice_len, seed=seed)
+    f = dict(pad=tf.pad_fp, tim=tf.time_fp, bin_off=tf.bin_off, n_slices=np.int64(tf.n_slices),
+             slice_len=np.int64(tf.slice_len), t0=tf.t0)
+    tmp = cache[:-4] + ".tmp%d.npz" % os.getpid()
+    np.savez(tmp, **f)
+    os.replace(tmp, cache)
+    log("time frame: %d collisions, %d slices, %d clusters in %.1f s" % (n_events, tf.n_slices, tf.n_clusters,
+                                                                          time.time() - t))
+    return f
 
 
 # ---------------------------------------------------------------------------------------------

@@ -158,6 +158,34 @@ int tpc_refit_grad(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, 
                    const float *weight, const float *anchor, int32_t error_model, double *sum_chi2, double *grad,
                    void *stream);
 
+/* Time-frame slice merge (arxiv 1712.09434 section 3, its outlook for continuous readout: a time
+ * frame of many overlapping collisions is cut along the drift-time axis, the slices are tracked
+ * one by one, and the track segments are merged afterwards).
+ *  - in: the clusters of n_events = n_slices consecutive slices of slice_len LSB of readout time,
+ *    in the batch layout (bin = (slice*n_sectors + sector)*n_rows + row) with slice-local times:
+ *    a cluster read out at time tau lies in slice floor(tau / slice_len) with time_fp = tau -
+ *    slice*slice_len.  1 <= slice_len <= round(z_max/lsb_cm) + 1.
+ *  - slice_trk: the tracks of every slice as tpc_track_batch writes them for `in` (trk_off,
+ *    trk_hits, ev_trk_off and n_tracks are read; device).  At most the context's chain capacity.
+ *  - frame (outputs, device): label [n_clusters] (frame track id or -1), trk_off [cap_tracks + 1],
+ *    trk_hits [cap_hits] (cluster indices; the hits of the chain's slice tracks, in chain order),
+ *    n_tracks [1], and ev_trk_off [2] = {0, n_tracks} if not NULL.  The other pointers are not
+ *    used and may be NULL.
+ * Rule: readout time falls outwards along a track, so the piece of a track in slice j+1 ends, at
+ * its outer end, where its piece in slice j begins.  The outer end of a slice-(j+1) track (its last
+ * hit and the hit 3 positions earlier, on (round(x_row/lsb), pad_fp, time_fp + slice_len)) is
+ * rotated into the frame of the first hit of a slice-j track when that lies in an adjacent sector
+ * of the same side (round(cos, sin 20 deg * 2^30), floor shifts), extrapolated linearly (floor
+ * division) to that track's first row (at most 2048 LSB away) and compared with the merge windows
+ * |dY|, |dZ| <= 192; D = dY^2 + dZ^2.  Mutual best pairs by (D, track index) are linked; a chain of
+ * links is one frame track, ordered by the index of its first slice track.  The links of the last
+ * call are what tpc_debug_copy 9 returns.
+ * Errors: INVALID_ARG, NOT_RESERVED, CUDA; device-side errors (CAPACITY: more slice tracks than the
+ * chain capacity, or more frame tracks or hits than cap_tracks / cap_hits; BOUNDS: a track offset
+ * or hit outside the clusters) via tpc_sync_status. */
+int tpc_merge_slices(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *slice_trk, int32_t slice_len,
+                     tpc_tracks *frame, void *stream);
+
 /* Set the launch shapes that later calls of this context use when they pass none (tpc_track_event,
  * tpc_refit_grad, and tpc_track_batch with tune == NULL); NULL restores the library defaults.
  * The values are copied.  Errors: INVALID_ARG (a value outside the bounds of tpc_tuning). */
@@ -174,7 +202,8 @@ const char *tpc_strerror(int code);
  * 0 up[N], 1 down[N] (neighbour links, -1 = none), 2 n_chains[1], 3 chain_start[C],
  * 4 chain_len[C], 5 cand_n[C], 6 cand_slots[C*n_rows] (cluster per row, -1 = miss, valid inside
  * the candidate's row range), 7 cand_rows[C] (first row | last row << 16), 8 seg_n[C] (kept hits,
- * 0 if rejected), 9 next[C] (merge successor or -1), 10 counters[16] (0 chains, 1 tracks, 2 hits,
+ * 0 if rejected), 9 next[C] (merge successor or -1; after tpc_merge_slices, the successor of every slice
+ * track in the next-earlier slice), 10 counters[16] (0 chains, 1 tracks, 2 hits,
  * 3 largest number of selection rounds), 11 the per-track records of the last tpc_refit_grad
  * (26 floats per track: weighted chi2, d/ds_vd, then 8 x (sector as int32 bits or -1, d/dd_k,
  * d/da_k); a track that was not fitted has chi2 0).  At most dst_bytes bytes are copied. */

@@ -73,6 +73,8 @@ def _load():
                                     ctypes.POINTER(tpc_tuning), vp]
     lib.tpc_refit_grad.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp, i32,
                                    vp, vp, vp]
+    lib.tpc_merge_slices.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), i32,
+                                     ctypes.POINTER(tpc_tracks), vp]
     lib.tpc_sync_status.argtypes = [vp, vp]
     lib.tpc_set_tuning.argtypes = [vp, ctypes.POINTER(tpc_tuning)]
     lib.tpc_strerror.argtypes = [ctypes.c_int]
@@ -230,6 +232,12 @@ class Context:
         check(_lib.tpc_refit_grad(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(theta), _ptr(weight),
                                   _ptr(anchor), int(error_model), _ptr(sum_chi2), _ptr(grad), _stream(stream)),
               "tpc_refit_grad")
+
+    def tpc_merge_slices(self, clusters, slice_tracks, slice_len, frame, stream=None):
+        """Join the tracks of consecutive time slices into frame tracks (see tpc_merge_slices)."""
+        cs, ss, fs = clusters.struct(), slice_tracks.struct(), frame.struct()
+        check(_lib.tpc_merge_slices(self.handle, ctypes.byref(cs), ctypes.byref(ss), int(slice_len), ctypes.byref(fs),
+                                    _stream(stream)), "tpc_merge_slices")
 
     def tpc_set_tuning(self, tuning=None):
         check(_lib.tpc_set_tuning(self.handle, ctypes.byref(tuning) if tuning is not None

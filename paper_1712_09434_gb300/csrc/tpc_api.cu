@@ -415,6 +415,27 @@ int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, co
     return cuda_err(cudaGetLastError());
 }
 
+int tpc_merge_slices(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *slice_trk, int32_t slice_len,
+                     tpc_tracks *frame, void *stream) {
+    if (!c) return TPC_ERR_INVALID_ARG;
+    int rc = validate_in(c, in);
+    if (rc) return rc;
+    if (!slice_trk || !slice_trk->trk_off || !slice_trk->trk_hits || !slice_trk->ev_trk_off || !slice_trk->n_tracks)
+        return TPC_ERR_INVALID_ARG;
+    if (!frame || !frame->label || !frame->trk_off || !frame->trk_hits || !frame->n_tracks || frame->cap_tracks < 1 ||
+        frame->cap_hits < 1)
+        return TPC_ERR_INVALID_ARG;
+    if (slice_len < 1 || slice_len > c->hgeom.zmax + 1) return TPC_ERR_INVALID_ARG;
+    Work W = make_work(c, in, frame, nullptr);
+    W.s_trk_off = slice_trk->trk_off;
+    W.s_trk_hits = slice_trk->trk_hits;
+    W.s_ev_trk_off = slice_trk->ev_trk_off;
+    W.s_n_tracks = slice_trk->n_tracks;
+    W.slice_len = slice_len;
+    launch_frame_merge(W, static_cast<cudaStream_t>(stream));
+    return cuda_err(cudaGetLastError());
+}
+
 int tpc_profile_enable(tpc_ctx *c, int enable) {
     if (!c) return TPC_ERR_INVALID_ARG;
     if (enable && !c->ev_pipe[0]) {

@@ -111,6 +111,9 @@ struct Work {
     int32_t *trk_n;           // [cap_tracks + 1] hits per track, then exclusive scan
     int32_t *trk_head;        // [cap_tracks] head segment of each track
     int32_t *trk_pack;        // [cap_hits * 2] (Y | Z<<16, sector | row<<16) per hit
+    // time-frame slice merge (S11): the per-slice tracks it reads (device)
+    const int32_t *s_trk_off, *s_trk_hits, *s_ev_trk_off, *s_n_tracks;
+    int slice_len;
     // scan scratch
     int32_t *scan_tmp;        // [scan_tmp_len]
     int scan_tmp_len;
@@ -126,6 +129,9 @@ enum {
     CNT_NTRACKS = 1,
     CNT_NHITS = 2,
     CNT_ROUNDS = 3,           // largest number of selection rounds of any sector
+    CNT_FRAME_N = 4,          // slice merge: slice tracks read, frame tracks, frame hits
+    CNT_FRAME_T = 5,
+    CNT_FRAME_H = 6,
     CNT_Q0 = 8,               // work-queue heads, one per kernel
 };
 
@@ -175,6 +181,7 @@ void launch_chains(const Work &W, cudaStream_t s);
 void launch_follow(const Work &W, cudaStream_t s);
 void launch_select(const Work &W, cudaStream_t s);
 void launch_merge(const Work &W, cudaStream_t s);
+void launch_frame_merge(const Work &W, cudaStream_t s);
 void launch_refit(const Work &W, const float *theta, cudaStream_t s);
 void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
                            bool grad, float *ck, float *rec, int32_t *order, int32_t *hist, cudaStream_t s);
