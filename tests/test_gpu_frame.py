@@ -40,7 +40,7 @@ def compare(g, o):
 
 @pytest.fixture(scope="module")
 def ctx():
-    c = _gpu.make_context(2_500_000, 64)
+    c = _gpu.make_context(6_000_000, 64)
     yield c
     c.close()
 
