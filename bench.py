@@ -400,6 +400,35 @@ def run_native(args, rank, world):
 
     ms_plain, _ = timed(plain, max(1, min(args.steps, 5)), 1)
 
+    # continuous readout: the same collisions overlaid in one readout stream at Poisson times (5 per
+    # drift length), cut into slices of one drift length, tracked as one batch of slices and
+    # joined by the slice merge
+    fr = make_frame(n_ev, seed0)
+    ns_f, L = int(fr["n_slices"]), int(fr["slice_len"])
+    cf = capi.Clusters.from_numpy(fr["pad"], fr["tim"], fr["bin_off"], ns_f)
+    tf_s = capi.Tracks(n_clusters, ns_f, cap_t, n_clusters)
+    tf_f = capi.Tracks(n_clusters, 1, cap_t, n_clusters)
+
+    def frame_step():
+        ctx.tpc_track_batch(cf, tf_s)
+        ctx.tpc_merge_slices(cf, tf_s, L, tf_f)
+
+    ms_frame, _ = timed(frame_step, max(3, min(args.steps, 10)), 3)
+    ms_fmerge, _ = timed(lambda: ctx.tpc_merge_slices(cf, tf_s, L, tf_f), 10, 3)
+    hs, hf = tf_s.to_host(), tf_f.to_host()
+    nxt = torch.empty(max(hs["n_tracks"], 1), dtype=torch.int32, device=dev)
+    ctx.tpc_debug_copy(9, nxt)
+    frame_out = {"value": n_clusters / (ms_frame * 1e-3), "unit": "clusters/s", "ms_per_frame": ms_frame,
+                 "slice_merge_ms": ms_fmerge, "collisions": n_ev, "collisions_per_drift_length": 5.0,
+                 "slices": ns_f, "slice_len_lsb": L, "clusters": int(fr["pad"].shape[0]),
+                 "slice_tracks": hs["n_tracks"], "links": int((nxt[:hs["n_tracks"]] >= 0).sum().item()),
+                 "frame_tracks": hf["n_tracks"],
+                 "step": "tpc_track_batch over the slices (CUDA graph) + tpc_merge_slices"}
+    del tf_s, tf_f, cf
+
+    # the single-event numbers below are other workloads: library default launch shapes
+    ctx.tpc_set_tuning(None)
+
     # adjoint cost on a central event with an injected calibration
     ev5 = synth.make_event(synth.calib_event())
     c5 = capi.Clusters.from_numpy(ev5.pad_fp, ev5.time_fp, ev5.bin_off, 1)
@@ -442,7 +471,7 @@ def run_native(args, rank, world):
 
     out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
                weighted_hits=weighted_hits,
-               calib=calib_out, single=single,
+               calib=calib_out, single=single, frame=frame_out,
                n_chains=n_chains, cand_hits=cand_hits)
     ctx.close()
     return out
@@ -523,6 +552,7 @@ def finish_native(args, res, world):
                     "tracks": res["n_tracks_c5"]},
         "calibration": res["calib"],
         "single_event": res["single"],
+        "time_frame": res["frame"],
         "stage_ms": stage_ms,
         "tuning": res["tuning"],
         "stage_algorithmic_gbs": {k: byts[k] / (stage_ms[k] * 1e-3) / 1e9 for k in stage_ms if k in byts and stage_ms[k] > 0},
