@@ -93,7 +93,9 @@ typedef struct {
  * most 256, 128, 256, 128, 1024, 512, 128, 128 by index), ctas_per_sm = CTAs per SM of the grid
  * (<= 64), chunk = work items taken per queue grab (<= 64; used by the following); for the neighbour
  * finding (index 1) chunk = 1 selects the variant that stages rows r+-1 of every bin in shared
- * memory by bulk copies (one CTA per bin) instead of reading them through L1 (one warp per bin).
+ * memory by bulk copies (one CTA per bin) instead of reading them through L1 (one warp per bin,
+ * lanes taking the bin's clusters in Z-slab order), and chunk = 2 the warp-per-bin variant whose
+ * lanes take the clusters in cluster (Y, Z) order.
  * Launch shapes never change results. */
 typedef struct {
     int32_t block[TPC_N_TUNE];

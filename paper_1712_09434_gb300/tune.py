@@ -23,7 +23,7 @@ KERNELS = ["grid", "links", "chains", "follow", "select", "merge", "refit", "ref
 # candidate (block, ctas_per_sm, chunk) per kernel; 0 = library default
 CANDIDATES = {
     "grid": dict(block=[64, 128, 256], ctas=[0, 8, 16, 32], chunk=[0]),
-    "links": dict(block=[64, 96, 128], ctas=[4, 6, 8, 10, 16], chunk=[0, 1]),   # 1: rows staged in smem
+    "links": dict(block=[64, 96, 128], ctas=[4, 6, 8, 10, 16], chunk=[0, 1, 2]),   # 0: slab order, 1: rows staged in smem, 2: cluster order
     "chains": dict(block=[64, 128, 256], ctas=[0, 8, 16, 32], chunk=[0]),
     "follow": dict(block=[64, 96, 128], ctas=[4, 8, 12, 16], chunk=[1, 2, 4]),
     "select": dict(block=[256, 512, 1024], ctas=[1, 2, 4], chunk=[0]),
