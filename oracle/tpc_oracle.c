@@ -7,7 +7,7 @@
  * below is declared here on its own, and a test compares the two sets of values.
  *
  * Steps follow the paper's tracker (section 3): cellular-automaton seeding on neighbouring pad
- * rows (neighbour finding, link cleaning, chains of "around 5 to 10 hits"), Kalman-filter
+ * rows (neighbour finding, link cleaning, seed chains of five to ten hits), Kalman-filter
  * track following and fitting, independent sectors whose segments are merged afterwards, and a
  * final track refit.  The paper fixes only this structure; every constant, rounding rule and
  * tie-break is a stated reading (listed in the design notes) and is written out here in plain
@@ -631,7 +631,7 @@ static void kf_rotate(const or_geom *g, or_kf *s, int k_new) {
     s->frame = k_new;
 }
 
-/* Helix step from local x to xh (section 3 "track following"; exact in the state): with C = kB q/pT,
+/* Helix step from local x to xh (section 3, the track following; exact in the state): with C = kB q/pT,
  * sin phi2 = sin phi + C dx, dy = dx (sin phi + sin phi2)/(cos phi + cos phi2), chord
  * L = dx sqrt(1 + T^2), arc = L asin(C L/2)/(C L/2), dz = tan lambda * arc.  F is the step Jacobian
  * d(state')/d(state), written in terms of T = tan of the mean direction (the derivatives of dz keep

@@ -1,5 +1,5 @@
 // S3 link cleaning and S4 chains (seeds of the cellular automaton; arxiv 1712.09434 section 3:
-// short track candidates of "around 5 to 10 hits" built from neighbour links).
+// short track candidates of five to ten hits built from neighbour links).
 //
 // A link c -> u is kept only if it is mutual (down[u] == c); both directions read the uncleaned
 // arrays.  The kept up-links are written once, with their 2- and 4-link successors (pointer
