@@ -91,3 +91,36 @@ def test_bounded_wait_times_out_and_reports():
     g = _gpu.run(ctx, _gpu.clusters_of(ev))
     assert g["n_tracks"] > 50
     ctx.close()
+
+
+def test_slice_merge_arguments_and_capacity():
+    """tpc_merge_slices: slice lengths outside [1, 32001] and missing outputs are invalid; a frame
+    output too small for the frame tracks is a capacity error on the device, with nothing written
+    beyond it."""
+    from paper_1712_09434_gb300 import synth
+    tf = synth.time_frame([_events.event("c1")], t0=[0], slice_len=16000)
+    ctx = _gpu.make_context(tf.n_clusters, tf.n_slices)
+    cl = capi.Clusters.from_numpy(tf.pad_fp, tf.time_fp, tf.bin_off, tf.n_slices)
+    st = capi.Tracks(tf.n_clusters, tf.n_slices, 4096, tf.n_clusters)
+    ctx.tpc_track_batch(cl, st)
+    assert ctx.tpc_sync_status() == capi.TPC_OK
+    fr = capi.Tracks(tf.n_clusters, 1, 4096, tf.n_clusters)
+    for bad_len in (0, -5, 32002):
+        with pytest.raises(capi.TpcError) as e:
+            ctx.tpc_merge_slices(cl, st, bad_len, fr)
+        assert e.value.code == capi.TPC_ERR_INVALID_ARG
+    nolabel = capi.Tracks(tf.n_clusters, 1, 4096, tf.n_clusters)
+    nolabel.label = None
+    with pytest.raises(capi.TpcError) as e:
+        ctx.tpc_merge_slices(cl, st, tf.slice_len, nolabel)
+    assert e.value.code == capi.TPC_ERR_INVALID_ARG
+    # room for 5 frame tracks only: the sentinel after trk_off[5] stays untouched
+    small = capi.Tracks(tf.n_clusters, 1, 5, tf.n_clusters)
+    small.trk_off = torch.full((8,), -7, dtype=torch.int32, device="cuda")
+    ctx.tpc_merge_slices(cl, st, tf.slice_len, small)
+    assert ctx.tpc_sync_status() == capi.TPC_ERR_CAPACITY
+    assert small.trk_off[6:].cpu().tolist() == [-7, -7]
+    ctx.tpc_merge_slices(cl, st, tf.slice_len, fr)
+    assert ctx.tpc_sync_status() == capi.TPC_OK
+    assert int(fr.n_tracks.item()) > 50
+    ctx.close()
