@@ -36,7 +36,7 @@ from paper_1712_09434_gb300 import synth  # noqa: E402
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
 # kernels of one step: tracking graph (grid 1, links 1, chains 8, follow 1, select 1, merge 17,
 # refit 1) + refit_grad (cluster bins 1, pack 1, length sort 3, forward and reverse pass 2, reduce 2)
-LAUNCHES_PER_STEP = 39
+LAUNCHES_PER_STEP = 43
 WORKLOAD = "batch-64-events-logU-100-20000-tracks-20pct-noise"
 
 
@@ -479,15 +479,15 @@ def run_native(args, rank, world):
 
 # floating-point operations per hit of the Kalman kernels, counted exactly from csrc/kf.cuh by
 # tests/kf_flop_count.cpp (a fused multiply-add counts two): the gradient kernel runs the forward
-# step twice (forward pass, then the recomputation from the checkpoints) and its adjoint once; the
-# tracking refit runs the square-root forward step
+# step once (storing every step's input state) and its adjoint once; the tracking refit runs the
+# square-root forward step
 FLOP_FWD, FLOP_ADJ, FLOP_SQRT_FWD = 461, 850, 434
 # FP32 peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def stage_flops(u):
-    return {"refit": FLOP_SQRT_FWD * u["n_hits"], "refit_grad": (2 * FLOP_FWD + FLOP_ADJ) * u["weighted_hits"]}
+    return {"refit": FLOP_SQRT_FWD * u["n_hits"], "refit_grad": (FLOP_FWD + FLOP_ADJ) * u["weighted_hits"]}
 
 
 # algorithmic bytes per stage (compulsory DRAM traffic of each stage's inputs and outputs)

@@ -95,7 +95,9 @@ typedef struct {
  * finding (index 1) chunk = 1 selects the variant that stages rows r+-1 of every bin in shared
  * memory by bulk copies (one CTA per bin) instead of reading them through L1 (one warp per bin,
  * lanes taking the bin's clusters in Z-slab order), and chunk = 2 the warp-per-bin variant whose
- * lanes take the clusters in cluster (Y, Z) order.
+ * lanes take the clusters in cluster (Y, Z) order; for the gradient kernel (index 7) chunk = 1
+ * recomputes the Kalman states of the reverse sweep from checkpoints every 16 steps instead of
+ * storing the input state of every step (100 B per hit of workspace; the default).
  * Launch shapes never change results. */
 typedef struct {
     int32_t block[TPC_N_TUNE];

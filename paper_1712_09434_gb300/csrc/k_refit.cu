@@ -18,11 +18,42 @@ namespace tpc {
 namespace {
 
 constexpr int CK_K = 16;           // steps between checkpoints
+constexpr int ST_SLACK = 4096;     // spare steps per lane for the chunk padding of the stored states
 constexpr int CK_WORDS = 25;       // x, p[5], P lower triangle[15], frame, rref, yref, zref
 constexpr int REC_SEC = 8;         // sector entries per track record
 constexpr int REC_WORDS = 2 + 3 * REC_SEC;
 constexpr int NPAR_MAX = 1 + 2 * MAX_SECTORS;
 constexpr int RED_T = 64;          // tracks per reduction block
+
+// Gradient workspace: checkpoints (MODE 1/2) | state after the last hit per track (MODE 3/4) |
+// chunk lengths, offsets and count | stored states (MODE 3/4).
+struct CkLayout {
+    float *ck;
+    float *fin;
+    int32_t *cl, *cb, *cn;
+    float *st;
+    long long cap_steps;   // chunk steps the stored states can hold
+};
+inline size_t ck_words_old(long long cap_hits, long long cap_tracks) {
+    return (size_t)(cap_hits / CK_K + 2 * cap_tracks + 1) * CK_WORDS;
+}
+inline size_t ck_words_fin(long long cap_tracks) { return (size_t)cap_tracks * CK_WORDS; }
+inline size_t ck_words_ints(long long cap_tracks) { return (size_t)(3 * (cap_tracks / 32 + 2) + 8); }
+inline size_t ck_words_st(long long cap_hits) { return (size_t)(cap_hits + 32ll * ST_SLACK) * CK_WORDS; }
+inline size_t ck_align(size_t w) { return (w + 31) & ~(size_t)31; }
+inline CkLayout ck_layout(float *base, long long cap_hits, long long cap_tracks) {
+    CkLayout L;
+    L.ck = base;
+    L.fin = base + ck_align(ck_words_old(cap_hits, cap_tracks));
+    const long long nch = cap_tracks / 32 + 2;
+    int32_t *ints = reinterpret_cast<int32_t *>(L.fin + ck_align(ck_words_fin(cap_tracks)));
+    L.cl = ints;
+    L.cb = ints + nch;
+    L.cn = ints + 2 * nch;
+    L.st = reinterpret_cast<float *>(ints) + ck_align(ck_words_ints(cap_tracks));
+    L.cap_steps = (cap_hits + 32ll * ST_SLACK) / 32;
+    return L;
+}
 
 struct FitGeo {
     kf::Geo<float> g;
@@ -313,15 +344,51 @@ __device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
     s.zref = src[24];
 }
 
+// Stored states (MODE 3/4): the input state of every step, interleaved by warp chunk so that the 32
+// lanes of a warp store and load each word with one coalesced access: word k of step q of the
+// track at position i of the length order lives at st[((cb[i/32] + q) * CK_WORDS + k) * 32 + i%32].
+__device__ __forceinline__ void st_store(float *st, long long step, int lane, const kf::State<float> &s) {
+    float *d = st + step * (CK_WORDS * 32) + lane;
+    d[0] = s.x;
+    for (int i = 0; i < 5; i++) d[(1 + i) * 32] = s.p[i];
+    int m = 6;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) d[(m++) * 32] = s.P[i][j];
+    d[21 * 32] = __int_as_float(s.frame);
+    d[22 * 32] = __int_as_float(s.rref);
+    d[23 * 32] = s.yref;
+    d[24 * 32] = s.zref;
+}
+__device__ __forceinline__ void st_load(const float *st, long long step, int lane, kf::State<float> &s) {
+    const float *d = st + step * (CK_WORDS * 32) + lane;
+    s.x = d[0];
+    for (int i = 0; i < 5; i++) s.p[i] = d[(1 + i) * 32];
+    int m = 6;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            s.P[i][j] = d[m * 32];
+            s.P[j][i] = d[m * 32];
+            m++;
+        }
+    s.frame = __float_as_int(d[21 * 32]);
+    s.rref = __float_as_int(d[22 * 32]);
+    s.yref = d[23 * 32];
+    s.zref = d[24 * 32];
+}
+
 // S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
-// MODE 0: forward pass only (objective).  MODE 1: forward pass that also stores the checkpoints and
-// the state after the last hit (frame -1 marks a track whose fit failed).  MODE 2: reverse sweep
-// from those states (the gradient part of the records).  Splitting the forward pass off lets it
-// run with fewer registers and more warps than the adjoint.
+// MODE 0: forward pass only (objective).  Gradient, default: MODE 3 runs the forward pass and stores
+// the input state of every step (100 B per hit, coalesced by warp chunk) and the state after the
+// last hit (frame -1 marks a track whose fit failed); MODE 4 runs the reverse sweep from the stored
+// states.  Gradient with less workspace: MODE 1 stores a checkpoint every CK_K steps, and MODE 2
+// recomputes each segment's states from its checkpoint before sweeping it backwards.  Both give
+// bit-identical results (the same operations in the same order).  Splitting the forward pass off
+// lets it run with fewer registers and more warps than the adjoint.
 template <int MODE>
-__global__ void __launch_bounds__(128, MODE == 2 ? 4 : 1) k_refit_grad(Work W, const double *theta, const float *weight,
-                                                    const float *anchor, int model, float *ck, float *rec,
-                                                    const int32_t *order) {
+__global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0 ? 1 : 7)) k_refit_grad(Work W, const double *theta,
+                                                    const float *weight, const float *anchor, int model,
+                                                    CkLayout L, float *rec, const int32_t *order) {
+    float *ck = L.ck;
     constexpr bool GRAD = MODE != 0;
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
@@ -349,10 +416,13 @@ __global__ void __launch_bounds__(128, MODE == 2 ? 4 : 1) k_refit_grad(Work W, c
         // checkpoints of track t: slots [off/CK_K + 2t, ... + ceil(n/CK_K)], the last one the state
         // after the last hit
         float *ckt = ck + ((size_t)(off / CK_K) + 2 * (size_t)t) * CK_WORDS;
-        float *ckend = ckt + (size_t)((n + CK_K - 1) / CK_K) * CK_WORDS;
+        float *ckend = MODE >= 3 ? L.fin + (size_t)t * CK_WORDS
+                                 : ckt + (size_t)((n + CK_K - 1) / CK_K) * CK_WORDS;
+        const long long step0 = MODE >= 3 ? (long long)L.cb[i >> 5] : 0;    // stored states of this lane
+        const int slane = i & 31;
         Anchor A{};
         bool use_anchor = false;
-        if (MODE != 2) {
+        if (MODE == 0 || MODE == 1 || MODE == 3) {
             kf::State<float> s;
             s.x = 0.f;
             s.rref = 0;
@@ -362,11 +432,16 @@ __global__ void __launch_bounds__(128, MODE == 2 ? 4 : 1) k_refit_grad(Work W, c
                 for (int j = 0; j < 5; j++) s.P[i][j] = i == j ? C0[i] : 0.f;
             float chi2 = 0.f;
             bool ok = n >= 3 && seed_track(W, G, th, off, n, s);
+            if (MODE == 3 && ok && step0 + n > L.cap_steps) {   // no room: reported, track dropped
+                set_status(W, ST_CAPACITY);
+                ok = false;
+            }
             HitRaw nxt = n >= 3 ? hit_raw(W, off + n - 1) : HitRaw{};
             for (int q = 0; ok && q < n; q++) {         // processing step q handles hit i = n-1-q
                 const HitRaw cur = nxt;
                 if (q + 1 < n) nxt = hit_raw(W, off + n - 2 - q);   // next hit's load in flight
-                if (GRAD && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
+                if (MODE == 1 && q % CK_K == 0) ck_store(ckt + (q / CK_K) * CK_WORDS, s);
+                if (MODE == 3) st_store(L.st, step0 + q, slane, s);
                 const HitT m = transform(G, th, ns, cur, model);
                 ok = kf::step_fwd(s, m.f, fg.g, chi2);
             }
@@ -385,7 +460,6 @@ __global__ void __launch_bounds__(128, MODE == 2 ? 4 : 1) k_refit_grad(Work W, c
         }
         // MODE 2: reverse sweep of a track whose forward pass succeeded
         if (n < 3 || __float_as_int(ckend[21]) < 0) continue;
-        float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
         use_anchor = anchor != nullptr && (A = load_anchor(anchor, t)).any();
         // reverse sweep, segment by segment from the last checkpoint
         kf::Adj<float> a;
@@ -403,53 +477,69 @@ __global__ void __launch_bounds__(128, MODE == 2 ? 4 : 1) k_refit_grad(Work W, c
                 anchor_bwd(st, j, A, fg.g, a);
             }
         }
-        for (int q0 = ((n - 1) / CK_K) * CK_K; q0 >= 0; q0 -= CK_K) {
-            const int q1 = min(q0 + CK_K, n);
-            kf::State<float> st;
-            ck_load(ckt + (q0 / CK_K) * CK_WORDS, st);
-            float dummy = 0.f;
-            HitRaw nx = hit_raw(W, off + n - 1 - q0);
-            for (int q = q0; q < q1; q++) {
-                const HitRaw cur = nx;
-                if (q + 1 < q1) nx = hit_raw(W, off + n - 2 - q);
-                ck_store(buf + (q - q0) * CK_WORDS, st);
-                const HitT m = transform(G, th, ns, cur, model);
-                kf::step_fwd(st, m.f, fg.g, dummy);
+        // one backward step from its input state sin_ (recomputed or stored), then the chain rule
+        auto bwd_step = [&](int q, const HitRaw &h, kf::State<float> &sin_) {
+            const HitT m = transform(G, th, ns, h, model);
+            float xb = 0.f, yb = 0.f, zb = 0.f, vyb = 0.f, vzb = 0.f;
+            kf::step_bwd(sin_, m.f, fg.g, a, &xb, &yb, &zb, &vyb, &vzb);
+            if (q == 0) {   // the seed position is this hit's (x, y, z)
+                xb += a.x;
+                yb += a.p[0];
+                zb += a.p[1];
             }
-            HitRaw hb = hit_raw(W, off + n - q1);
-            for (int q = q1 - 1; q >= q0; q--) {
-                const HitRaw h = hb;
-                if (q > q0) hb = hit_raw(W, off + n - q);
-                const HitT m = transform(G, th, ns, h, model);
-                float xb = 0.f, yb = 0.f, zb = 0.f, vyb = 0.f, vzb = 0.f;
-                kf::State<float> sin_;
-                ck_load(buf + (q - q0) * CK_WORDS, sin_);
-                kf::step_bwd(sin_, m.f, fg.g, a, &xb, &yb, &zb, &vyb, &vzb);
-                if (q == 0) {   // the seed position is this hit's (x, y, z)
-                    xb += a.x;
-                    yb += a.p[0];
-                    zb += a.p[1];
-                }
-                // chain rule through S0
-                if (h.k != cur_sec) {
-                    if (cur_sec >= 0) {
-                        if (n_ent < REC_SEC) {
-                            ent_s[n_ent] = cur_sec;
-                            ent_d[n_ent] = gd.value();
-                            ent_a[n_ent] = ga.value();
-                        } else {
-                            set_status(W, ST_CAPACITY);
-                        }
-                        n_ent++;
+            // chain rule through S0
+            if (h.k != cur_sec) {
+                if (cur_sec >= 0) {
+                    if (n_ent < REC_SEC) {
+                        ent_s[n_ent] = cur_sec;
+                        ent_d[n_ent] = gd.value();
+                        ent_a[n_ent] = ga.value();
+                    } else {
+                        set_status(W, ST_CAPACITY);
                     }
-                    cur_sec = h.k;
-                    gd = Kahan();
-                    ga = Kahan();
+                    n_ent++;
                 }
-                // model 1: vz = sigma^2 s_vd^2, vy = sigma^2 (1 + a_k g')^2
-                gs.add(zb * m.dzds + (model == 1 ? vzb * (2.f * SIGMA2) * m.jz : 0.f));
-                gd.add(zb);
-                ga.add((xb * m.xr + yb * m.yraw + (model == 1 ? vyb * (2.f * SIGMA2) * m.jy : 0.f)) * m.gp);
+                cur_sec = h.k;
+                gd = Kahan();
+                ga = Kahan();
+            }
+            // model 1: vz = sigma^2 s_vd^2, vy = sigma^2 (1 + a_k g')^2
+            gs.add(zb * m.dzds + (model == 1 ? vzb * (2.f * SIGMA2) * m.jz : 0.f));
+            gd.add(zb);
+            ga.add((xb * m.xr + yb * m.yraw + (model == 1 ? vyb * (2.f * SIGMA2) * m.jy : 0.f)) * m.gp);
+        };
+        if constexpr (MODE == 2) {      // segment by segment from the last checkpoint
+            float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
+            for (int q0 = ((n - 1) / CK_K) * CK_K; q0 >= 0; q0 -= CK_K) {
+                const int q1 = min(q0 + CK_K, n);
+                kf::State<float> st;
+                ck_load(ckt + (q0 / CK_K) * CK_WORDS, st);
+                float dummy = 0.f;
+                HitRaw nx = hit_raw(W, off + n - 1 - q0);
+                for (int q = q0; q < q1; q++) {
+                    const HitRaw cur = nx;
+                    if (q + 1 < q1) nx = hit_raw(W, off + n - 2 - q);
+                    ck_store(buf + (q - q0) * CK_WORDS, st);
+                    const HitT m = transform(G, th, ns, cur, model);
+                    kf::step_fwd(st, m.f, fg.g, dummy);
+                }
+                HitRaw hb = hit_raw(W, off + n - q1);
+                for (int q = q1 - 1; q >= q0; q--) {
+                    const HitRaw h = hb;
+                    if (q > q0) hb = hit_raw(W, off + n - q);
+                    kf::State<float> sin_;
+                    ck_load(buf + (q - q0) * CK_WORDS, sin_);
+                    bwd_step(q, h, sin_);
+                }
+            }
+        } else {                        // MODE 4: the stored input state of every step
+            HitRaw hb = hit_raw(W, off);
+            for (int q = n - 1; q >= 0; q--) {
+                const HitRaw h = hb;
+                if (q > 0) hb = hit_raw(W, off + n - q);
+                kf::State<float> sin_;
+                st_load(L.st, step0 + q, slane, sin_);
+                bwd_step(q, h, sin_);
             }
         }
         if (cur_sec >= 0) {
@@ -563,6 +653,27 @@ __global__ void k_len_scatter(Work W, int32_t *hist, int32_t *order) {
     }
 }
 
+// Longest track of every warp chunk (32 consecutive positions) of the length order, and the
+// number of chunks: the chunk offsets of the stored states are their exclusive scan.
+__global__ void k_chunk_len(Work W, const int32_t *order, CkLayout L) {
+    const int nt = n_tracks_of(W);
+    const int nch = (nt + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *L.cn = nch;
+    for (int c = gw; c < nch; c += nw) {
+        const int i = 32 * c + lane;
+        int len = 0;
+        if (i < nt) {
+            const int t = order[i];
+            len = max(W.trk_off[t + 1] - W.trk_off[t], 0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+        if (lane == 0) L.cl[c] = len;
+    }
+}
+
 // Bin of every cluster (warp per bin), into a workspace array of N words.
 __global__ void k_cluster_bins(Work W, int32_t *cbin) {
     const int lane = threadIdx.x & 31;
@@ -606,7 +717,10 @@ void launch_pack_hits(const Work &W, cudaStream_t s) {
     k_pack_hits<<<W.sm_count * 4, 256, 0, s>>>(W, W.clen);
 }
 
-int refit_ck_words(int cap_hits, int cap_tracks) { return (cap_hits / CK_K + 2 * cap_tracks + 1) * CK_WORDS; }
+size_t refit_ck_words(long long cap_hits, long long cap_tracks) {
+    return ck_align(ck_words_old(cap_hits, cap_tracks)) + ck_align(ck_words_fin(cap_tracks)) +
+           ck_align(ck_words_ints(cap_tracks)) + ck_words_st(cap_hits);
+}
 int refit_rec_words(int cap_tracks) { return cap_tracks * REC_WORDS; }
 int refit_part_doubles(int cap_tracks, int ns) { return ((cap_tracks + RED_T - 1) / RED_T + 1) * (2 * ns + 2); }
 
@@ -618,20 +732,28 @@ void launch_refit(const Work &W, const float *theta, cudaStream_t s) {
 }
 
 void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
-                           bool grad, float *ck, float *rec, int32_t *order, int32_t *hist, cudaStream_t s) {
+                           bool grad, float *ck, long long ck_hits, long long ck_tracks, float *rec, int32_t *order,
+                           int32_t *hist, cudaStream_t s) {
     const int block = W.tune.block[7] > 0 ? W.tune.block[7] : 128;
     const int grid = W.tune.grid[7] > 0 ? W.tune.grid[7] : W.sm_count * 8;
+    const CkLayout L = ck_layout(ck, ck_hits, ck_tracks);
     cudaMemsetAsync(hist, 0, sizeof(int32_t) * LEN_BUCKETS, s);
     cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
     k_len_hist<<<W.sm_count * 4, 256, 0, s>>>(W, hist);
     k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
     k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
-    if (grad) {
-        k_refit_grad<1><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+    if (grad && W.tune.chunk[7] != 1) {     // every step's input state stored, no recomputation
+        k_chunk_len<<<W.sm_count * 4, 256, 0, s>>>(W, order, L);
+        scan_exclusive(L.cl, L.cb, (int)(ck_tracks / 32 + 1), L.cn, L.cn + 1, W.scan_tmp, W.scan_tmp_len, s);
+        k_refit_grad<3><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
         cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
-        k_refit_grad<2><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+        k_refit_grad<4><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
+    } else if (grad) {                      // checkpoints every CK_K steps, recomputation (less memory)
+        k_refit_grad<1><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
+        cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
+        k_refit_grad<2><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
     } else {
-        k_refit_grad<0><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, ck, rec, order);
+        k_refit_grad<0><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
     }
 }
 

@@ -116,7 +116,7 @@ size_t layout(tpc_ctx *c, char *base) {
     w.scan_tmp_len = (int)scan_len;
     carve(cur, w.counters, 64);
     carve(cur, w.status, 8);
-    carve(cur, c->ck, (size_t)refit_ck_words((int)N, (int)C));
+    carve(cur, c->ck, refit_ck_words((long long)N, (long long)C));
     carve(cur, c->rec, (size_t)refit_rec_words((int)C));
     carve(cur, c->part, (size_t)refit_part_doubles((int)C, c->hgeom.n_sectors));
     carve(cur, c->order, C + 1);
@@ -405,7 +405,8 @@ int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, co
     TPC_CUDA(cudaMemcpyAsync(W.counters + CNT_NTRACKS, trk->n_tracks, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     launch_pack_hits(W, s);
     if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[1], s));
-    launch_refit_grad_fit(W, theta, weight, anchor, error_model, grad != nullptr, c->ck, c->rec, c->order, c->lhist, s);
+    launch_refit_grad_fit(W, theta, weight, anchor, error_model, grad != nullptr, c->ck, (long long)c->max_clusters + 1,
+                          (long long)c->cap_chains + 1, c->rec, c->order, c->lhist, s);
     if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[2], s));
     launch_refit_grad_reduce(W, sum_chi2, grad, c->rec, c->part, s);
     if (prof) {

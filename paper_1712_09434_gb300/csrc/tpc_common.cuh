@@ -184,10 +184,11 @@ void launch_merge(const Work &W, cudaStream_t s);
 void launch_frame_merge(const Work &W, cudaStream_t s);
 void launch_refit(const Work &W, const float *theta, cudaStream_t s);
 void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
-                           bool grad, float *ck, float *rec, int32_t *order, int32_t *hist, cudaStream_t s);
+                           bool grad, float *ck, long long ck_hits, long long ck_tracks, float *rec, int32_t *order,
+                           int32_t *hist, cudaStream_t s);
 void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,
                               cudaStream_t s);
-int refit_ck_words(int cap_hits, int cap_tracks);
+size_t refit_ck_words(long long cap_hits, long long cap_tracks);
 int refit_rec_words(int cap_tracks);
 int refit_part_doubles(int cap_tracks, int ns);
 void launch_pack_hits(const Work &W, cudaStream_t s);

@@ -279,7 +279,8 @@ def test_launch_shapes_do_not_change_results(ctx):
               "select": (256, 1, 0), "merge": (512, 4, 0), "refit": (64, 2, 0), "refit_grad": (64, 2, 0)}
     staged = dict(shapes, links=(128, 8, 1))        # neighbour rows staged in shared memory
     slab = dict(shapes, links=(96, 16, 2))          # lanes in cluster order (default: Z-slab order)
-    for sh in (shapes, staged, slab):
+    ckpt = dict(shapes, refit_grad=(128, 4, 1))     # gradient from checkpoints (default: stored states)
+    for sh in (shapes, staged, slab, ckpt):
         ctx.tpc_set_tuning(tune.to_struct(sh))
         try:
             g1, s1, gr1 = run_all()
