@@ -168,7 +168,8 @@ int tpc_refit_grad(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, 
  *  - in: the clusters of n_events = n_slices consecutive slices of slice_len LSB of readout time,
  *    in the batch layout (bin = (slice*n_sectors + sector)*n_rows + row) with slice-local times:
  *    a cluster read out at time tau lies in slice floor(tau / slice_len) with time_fp = tau -
- *    slice*slice_len.  1 <= slice_len <= round(z_max/lsb_cm) + 1.
+ *    slice*slice_len < slice_len (a track starting at a later time is a BOUNDS error).
+ *    1 <= slice_len <= round(z_max/lsb_cm) + 1.
  *  - slice_trk: the tracks of every slice as tpc_track_batch writes them for `in` (trk_off,
  *    trk_hits, ev_trk_off and n_tracks are read; device).  At most the context's chain capacity.
  *  - frame (outputs, device): label [n_clusters] (frame track id or -1), trk_off [cap_tracks + 1],

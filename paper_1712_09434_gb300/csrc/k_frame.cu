@@ -73,6 +73,7 @@ __global__ void k_frame_ends(Work W) {
         const int hL = W.s_trk_hits[o1 - 1];
         if (h0 < 0 || h0 >= W.n_clusters || hL < 0 || hL >= W.n_clusters) { set_status(W, ST_BOUNDS); continue; }
         const int j = slice_of(W, t);
+        if (W.tim[h0] >= W.slice_len) set_status(W, ST_BOUNDS);   // a slice-local time past the slice
         const int b0 = bin_of(W.bin_off, W.nbins, h0) % nbe;
         const int r0 = b0 % W.nr, k0 = b0 / W.nr;
         W.inend[t] = make_int4(g.xtab[r0], W.pad[h0], W.tim[h0], k0);
@@ -136,6 +137,16 @@ __global__ void k_frame_match(Work W) {
             }
             const long long dxs = x2 - x1;
             if (dxs <= 0) continue;
+            // The extrapolated time is monotonic in XT, so its range over the reach |XT - x2| <=
+            // MERGE_XMAX is that of the two ends.  A slice-j track starts at a time in [0, slice_len);
+            // if the window around every extrapolated time misses that range, no T can match (the
+            // usual case: S is a whole track whose outer end lies far from the slice start).
+            {
+                const long long za = p1.z + floor_div_pos((x2 - MERGE_XMAX - x1) * (long long)(p2.z - p1.z), dxs);
+                const long long zb = p1.z + floor_div_pos((x2 + MERGE_XMAX - x1) * (long long)(p2.z - p1.z), dxs);
+                const long long zmin = za < zb ? za : zb, zmax = za < zb ? zb : za;
+                if (zmin - W_MERGE > W.slice_len - 1 || zmax + W_MERGE < 0) continue;
+            }
             // rows whose plane is within MERGE_XMAX of the extrapolation start (one row of margin;
             // the exact test is below)
             int r_lo = (int)floorf((float)(x2 - MERGE_XMAX - g.xtab[0]) / pitch) - 1;
