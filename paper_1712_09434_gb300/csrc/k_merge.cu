@@ -57,6 +57,7 @@ __global__ void k_merge_ends(Work W) {
         const int iL = (cnt - 1) % (MERGE_BACK + 1), iB = (cnt - 1 - MERGE_BACK) % (MERGE_BACK + 1);
         const int hL = ring_h[iL], rL = ring_r[iL], hB = ring_h[iB], rB = ring_r[iB];
         W.inend[t] = make_int4(g.xtab[rf], W.pad[first], W.tim[first], sector);
+        atomicMax(W.sec_ymax + W.chain_bin[t] / (W.ns * W.nr) * W.ns + sector, abs((int)W.pad[first]));
         atomicAdd(W.bin_cnt + (W.chain_bin[t] - W.chain_bin[t] % W.nr) + rf, 1);
         W.outend[2 * t] = make_int4(g.xtab[rB], W.pad[hB], W.tim[hB], sector);
         W.outend[2 * t + 1] = make_int4(g.xtab[rL], W.pad[hL], W.tim[hL], 0);
@@ -109,6 +110,17 @@ __global__ void k_merge_match(Work W) {
             const long long y2 = (-sgn * X2 * g.s30 + Y2 * g.c30) >> 30;
             const long long dxs = x2 - x1;
             if (dxs <= 0) continue;
+            // The extrapolated Y is monotonic in XT, so its range over the reach |XT - x2| <=
+            // MERGE_XMAX is that of the two ends.  If the window around it misses the range of the
+            // first-hit Y of every segment of sector kt, no T there can match (the usual case: S
+            // ends away from the edge that faces kt).
+            {
+                const long long ya = y1 + floor_div_pos((x2 - MERGE_XMAX - x1) * (y2 - y1), dxs);
+                const long long yb = y1 + floor_div_pos((x2 + MERGE_XMAX - x1) * (y2 - y1), dxs);
+                const long long ymin = ya < yb ? ya : yb, ymx = ya < yb ? yb : ya;
+                const long long bound = W.sec_ymax[ev * W.ns + kt];
+                if (ymin - W_MERGE > bound || ymx + W_MERGE < -bound) continue;
+            }
             const int b0 = (ev * W.ns + kt) * W.nr;
             // rows whose plane is within MERGE_XMAX of the extrapolation start (one row of margin;
             // the exact test is below)
@@ -255,6 +267,7 @@ void launch_merge(const Work &W, cudaStream_t s) {
     const int block = W.tune.block[5] > 0 ? W.tune.block[5] : 128;
     const int grid = W.tune.grid[5] > 0 ? W.tune.grid[5] : W.sm_count * 8;
     cudaMemsetAsync(W.bin_cnt, 0, sizeof(int32_t) * (W.nbins + 1), s);
+    cudaMemsetAsync(W.sec_ymax, 0, sizeof(int32_t) * (size_t)W.n_events * W.ns, s);
     k_merge_ends<<<grid, block, 0, s>>>(W);
     scan_exclusive(W.bin_cnt, W.mrg_off, W.nbins, nullptr, nullptr, W.scan_tmp, W.scan_tmp_len, s);
     cudaMemsetAsync(W.bin_cnt, 0, sizeof(int32_t) * (W.nbins + 1), s);

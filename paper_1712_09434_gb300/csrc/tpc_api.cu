@@ -104,6 +104,7 @@ size_t layout(tpc_ctx *c, char *base) {
     carve(cur, w.mrg_off, nb + 1);
     carve(cur, w.mrg_list, C);
     carve(cur, w.outend, 2 * C);
+    carve(cur, w.sec_ymax, (size_t)c->max_events * c->hgeom.n_sectors + 1);
     carve(cur, w.head, C);
     carve(cur, w.head_id, C + 1);
     carve(cur, w.trk_n, C + 1);

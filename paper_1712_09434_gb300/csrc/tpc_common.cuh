@@ -106,6 +106,7 @@ struct Work {
     int32_t *mrg_off;         // [nbins + 1] accepted segments per (event, sector, first row)
     int32_t *mrg_list;        // [cap_chains] segment indices in mrg_off order
     int4 *outend;             // [cap_chains * 2] (X1, Y1, Z1, sector), (X2, Y2, Z2, -) of the outer end
+    int32_t *sec_ymax;        // [max_events * n_sectors] largest |Y| of a segment's first kept hit
     int32_t *head;            // [cap_chains] 1 if the segment starts a merged track
     int32_t *head_id;         // [cap_chains + 1] exclusive scan of head = track id
     int32_t *trk_n;           // [cap_tracks + 1] hits per track, then exclusive scan
