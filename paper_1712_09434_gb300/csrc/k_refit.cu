@@ -4,10 +4,10 @@
 //
 // One thread per track (the paper's one-thread-per-track mapping).  The seed is the circle
 // through the first, middle and last hit at the nominal calibration, so it does not depend on
-// theta; the fit runs from the last hit to the first.  The adjoint stores the input state of every
-// K-th step (checkpoints) during the forward pass; the reverse sweep restores each checkpoint,
-// recomputes the K states of its segment and walks them backwards, so per-row states are
-// recomputed rather than stored for the whole track.  Per-track chi2 and gradient contributions
+// theta; the fit runs from the last hit to the first.  The adjoint's forward pass stores the input
+// state of every step (coalesced by warp chunk) and the reverse sweep walks them backwards; a
+// low-memory form stores every K-th state (checkpoints) instead and recomputes each segment before
+// walking it backwards (same results, bit for bit).  Per-track chi2 and gradient contributions
 // (s_vd, and (d_k, a_k) for every sector the track visits) are written as records and summed in
 // FP64 in a fixed order (deterministic).
 #include "kf.cuh"
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0
         // MODE 2: reverse sweep of a track whose forward pass succeeded
         if (n < 3 || __float_as_int(ckend[21]) < 0) continue;
         use_anchor = anchor != nullptr && (A = load_anchor(anchor, t)).any();
-        // reverse sweep, segment by segment from the last checkpoint
+        // reverse sweep from the last hit
         kf::Adj<float> a;
         kf::adj_zero(a);
         Kahan gs, gd, ga;       // compensated FP32 sums over the hits of the track
