@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0
             }
             continue;
         }
-        // MODE 2: reverse sweep of a track whose forward pass succeeded
+        // MODE 2 / 4: reverse sweep of a track whose forward pass succeeded
         if (n < 3 || __float_as_int(ckend[21]) < 0) continue;
         use_anchor = anchor != nullptr && (A = load_anchor(anchor, t)).any();
         // reverse sweep from the last hit
