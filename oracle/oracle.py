@@ -194,11 +194,12 @@ def track_frame(pad, tim, bin_off, n_slices, slice_len, g=None):
     gg = g if g is not None else geometry()
     nbe = gg.n_sectors * gg.n_rows
     bin_off = np.ascontiguousarray(bin_off, np.int64)
-    offs, hits, ev_trk_off = [np.zeros(1, np.int64)], [], [0]
+    offs, hits, ev_trk_off, n_hits = [np.zeros(1, np.int64)], [], [0], 0
     for j in range(n_slices):
         a, b = int(bin_off[j * nbe]), int(bin_off[(j + 1) * nbe])
         o = track_event(pad[a:b], tim[a:b], (bin_off[j * nbe:(j + 1) * nbe + 1] - a).astype(np.int32), g)
-        offs.append(o["trk_off"][1:].astype(np.int64) + (offs[-1][-1] if len(offs[-1]) else 0))
+        offs.append(o["trk_off"][1:].astype(np.int64) + n_hits)
+        n_hits += int(o["trk_off"][-1])
         hits.append(o["trk_hits"].astype(np.int64) + a)
         ev_trk_off.append(ev_trk_off[-1] + len(o["trk_off"]) - 1)
     trk_off = np.concatenate(offs).astype(np.int32)

@@ -132,3 +132,22 @@ def test_frame_tracks_partition_the_slice_tracks(frame6):
     s = np.nonzero(f["next"] >= 0)[0]
     assert np.all(sl[s] == sl[f["next"][s]] + 1)
     assert len(np.unique(f["next"][s])) == len(s)
+
+
+def test_frame_with_empty_slices_keeps_offsets():
+    """Two collisions far apart (a whole number of slices between them, so that each is cut where
+    it would be cut alone) leave empty slices in the middle of the frame: the frame holds exactly
+    the slice tracks and frame tracks of the two collisions tracked alone."""
+    evs = [synth.make_event(synth.EventConfig(n_tracks=300, noise_frac=0.1, seed=s)) for s in (41, 42)]
+
+    def frame(events, t0):
+        tf = synth.time_frame(events, slice_len=16000, t0=t0)
+        return tf, O.track_frame(tf.pad_fp, tf.time_fp, tf.bin_off, tf.n_slices, tf.slice_len)
+
+    tf, f = frame(evs, [0, 96000])
+    assert np.any(np.diff(tf.ev_off) == 0)
+    assert np.all(np.diff(f["trk_off"]) >= 10)
+    alone = [frame([ev], [0])[1] for ev in evs]
+    assert len(f["trk_off"]) - 1 == sum(len(a["trk_off"]) - 1 for a in alone)
+    assert len(f["ftrk_off"]) - 1 == sum(len(a["ftrk_off"]) - 1 for a in alone)
+    assert len(f["trk_hits"]) == sum(len(a["trk_hits"]) for a in alone)

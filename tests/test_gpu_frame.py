@@ -97,3 +97,17 @@ def test_full_size_frame_sampled_slices():
     gn = g["next"][t1:t2]
     on = o["next"][t1 - t0:]
     np.testing.assert_array_equal(np.where(gn >= 0, gn - t0, -1), on)
+
+
+def test_frames_with_empty_slices(ctx):
+    """Collisions far apart leave whole slices empty; an empty frame has no tracks at all."""
+    evs = [synth.make_event(synth.EventConfig(n_tracks=300, noise_frac=0.1, seed=s)) for s in (41, 42)]
+    tf = synth.time_frame(evs, slice_len=16000, t0=[0, 96000])
+    o = O.track_frame(tf.pad_fp, tf.time_fp, tf.bin_off, tf.n_slices, tf.slice_len)
+    assert np.any(np.diff(tf.ev_off) == 0)                      # some slices hold no cluster
+    g = run_frame(ctx, tf.pad_fp, tf.time_fp, tf.bin_off, tf.n_slices, tf.slice_len)
+    compare(g, o)
+    n_sl = 5
+    empty_bo = np.zeros(n_sl * synth.N_SECTORS * synth.N_ROWS + 1, np.int32)
+    e = run_frame(ctx, np.zeros(0, np.int16), np.zeros(0, np.uint16), empty_bo, n_sl, 32000)
+    assert len(e["ftrk_off"]) == 1 and len(e["ftrk_hits"]) == 0 and list(e["fevo"][:2]) == [0, 0]
