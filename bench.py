@@ -349,51 +349,65 @@ def run_native(args, rank, world):
     h2d = h_pad.numel() * 2 + h_tim.numel() * 2 + h_bo.numel() * 4
     d2h = (h_label.numel() + h_off.numel() + h_hits.numel()) * 4 + h_par.numel() * 4 + h_red.numel() * 8
 
-    # pipelined: the two contexts of the timed steps, each with its own inputs, outputs and compute
-    # stream; the copies of a step's inputs and of its results run on copy streams while the other
-    # context computes
+    # pipelined: the two contexts of the timed steps take the steps in turn, each on its own compute
+    # stream.  Every context has two input buffer sets, so that a step's inputs are copied in while
+    # the context's previous step still computes, and its results are copied to a device staging
+    # set right after its compute (a fast device copy), from which they go to the host on a copy
+    # stream while the next steps compute: no context waits for a host transfer.
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    cls = [cl, cl2]
+
+    def dev_inputs():
+        return capi.Clusters(torch.empty_like(d_pad), torch.empty_like(d_tim), torch.empty_like(d_bo), n_ev)
+
+    cls = [[cl, dev_inputs()], [cl2, dev_inputs()]]
     trs = [tr, tr2]
     reds = [(s_chi2, grad), (s_chi2_2, grad_2)]
-    h_outs = [(h_label, h_off, h_hits, h_par, h_red)] + [tuple(torch.empty_like(x).pin_memory() for x in
-                                                              (h_label, h_off, h_hits, h_par, h_red))]
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_out = [torch.cuda.Event(), torch.cuda.Event()]
+    out_views = lambda t_: (t_.label[:n_clusters], t_.trk_off[:cap_t + 1], t_.trk_hits[:n_clusters],
+                            t_.par[:cap_t * 5])
+    stage = [[tuple(torch.empty_like(x) for x in out_views(tr)) + (torch.empty(74, dtype=torch.float64, device=dev),)
+              for _ in range(2)] for _ in range(2)]
+    h_outs = [[(h_label, h_off, h_hits, h_par, h_red)] +
+              [tuple(torch.empty_like(x).pin_memory() for x in (h_label, h_off, h_hits, h_par, h_red))],
+              [tuple(torch.empty_like(x).pin_memory() for x in (h_label, h_off, h_hits, h_par, h_red))
+               for _ in range(2)]]
+    ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
+    ev_comp = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
+    ev_out = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
 
-    def e2e_pipelined(n_steps):
-        for k in range(n_steps):
-            b = k % 2
-            c, t_, (sc, gr), (hl, ho, hh, hp, hr) = cls[b], trs[b], reds[b], h_outs[b]
-            with torch.cuda.stream(s_in):                 # inputs of step k (buffer free once step k-2 ran)
-                s_in.wait_event(ev_comp[b])
+    def e2e_pipelined(n_steps, first=0):
+        for k in range(first, first + n_steps):
+            b, j = k % 2, (k // 2) % 2                    # context, buffer set of this context
+            c, t_, (sc, gr) = cls[b][j], trs[b], reds[b]
+            st, ho = stage[b][j], h_outs[b][j]
+            cx, cs = lanes[b][0], lanes[b][5]
+            with torch.cuda.stream(s_in):                 # inputs (free once this set's last step ran)
+                s_in.wait_event(ev_comp[b][j])
                 c.pad_fp.copy_(h_pad, non_blocking=True)
                 c.time_fp.copy_(h_tim, non_blocking=True)
                 c.bin_off.copy_(h_bo, non_blocking=True)
-                ev_in[b].record(s_in)
-            cx, cs = lanes[b][0], lanes[b][5]
-            cs.wait_event(ev_in[b])
-            cs.wait_event(ev_out[b])                      # results of step k-2 copied out
+                ev_in[b][j].record(s_in)
+            cs.wait_event(ev_in[b][j])
             cx.tpc_track_batch(c, t_, stream=cs)
             cx.tpc_refit_grad(c, t_, theta, sc, gr, w_batch, stream=cs)
-            ev_comp[b].record(cs)
-            with torch.cuda.stream(s_out):                # results of step k
-                s_out.wait_event(ev_comp[b])
-                hl.copy_(t_.label[:n_clusters], non_blocking=True)
-                ho.copy_(t_.trk_off[:cap_t + 1], non_blocking=True)
-                hh.copy_(t_.trk_hits[:n_clusters], non_blocking=True)
-                hp.copy_(t_.par[:cap_t * 5], non_blocking=True)
-                hr[:1].copy_(sc, non_blocking=True)
-                hr[1:].copy_(gr, non_blocking=True)
-                ev_out[b].record(s_out)
+            cs.wait_event(ev_out[b][j])                   # this staging set is on the host already
+            with torch.cuda.stream(cs):                   # results to device staging
+                for dst, src in zip(st[:4], out_views(t_)):
+                    dst.copy_(src, non_blocking=True)
+                st[4][:1].copy_(sc, non_blocking=True)
+                st[4][1:].copy_(gr, non_blocking=True)
+            ev_comp[b][j].record(cs)
+            with torch.cuda.stream(s_out):                # staging to the host
+                s_out.wait_event(ev_comp[b][j])
+                for dst, src in zip(ho, st):
+                    dst.copy_(src, non_blocking=True)
+                ev_out[b][j].record(s_out)
         stream.wait_stream(s_in)
         for lane_ in lanes:
             stream.wait_stream(lane_[5])
         stream.wait_stream(s_out)
 
-    n_pipe = max(4, min(args.steps, 20))
-    e2e_pipelined(2)                       # warm: both buffer sets captured once
+    n_pipe = max(8, min(args.steps, 40))
+    e2e_pipelined(4)                       # warm: every buffer set of both contexts captured once
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -401,7 +415,11 @@ def run_native(args, rank, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    e2e_pipelined(n_pipe)
+    for lane_ in lanes:
+        lane_[5].wait_event(e0)
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    e2e_pipelined(n_pipe, first=4)
     e1.record(stream)
     e1.synchronize()
     ms_e2e = e0.elapsed_time(e1) / n_pipe
@@ -610,8 +628,9 @@ def finish_native(args, res, world):
         "stage_tflops": {k: flops[k] / (stage_ms[k] * 1e-3) / 1e12 for k in flops if stage_ms.get(k, 0) > 0},
         "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"],
-                "form": "through the binding from pinned host buffers; two buffer sets, input and output "
-                        "copies on their own streams overlapping the compute of the neighbouring steps",
+                "form": "through the binding from pinned host buffers; two contexts taking the steps in turn, "
+                        "two input sets per context, results staged on the device; host copies on their "
+                        "own streams overlapping the compute",
                 "sequential_value": n_cl_total / (res["ms_e2e_seq"] * 1e-3)},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": res["clocks"],
