@@ -298,6 +298,18 @@ def constants():
     return dict(zip(names, buf[:k].tolist()))
 
 
+def merge_decide(ks, s_end, kt, t_first, g=None):
+    """S7 decision on integer end points: s_end = (X1, Y1, Z1, X2, Y2, Z2) of S (the hit MERGE_BACK
+    positions before its outer end, and its last hit) in the frame of sector ks; t_first = (XT, YT,
+    ZT) of T's first hit in the frame of sector kt.  Returns D = dY^2 + dZ^2 on a match, else None."""
+    D = ctypes.c_int64(-1)
+    se = np.ascontiguousarray(s_end, np.int64)
+    tf = np.ascontiguousarray(t_first, np.int64)
+    ok = lib().or_merge_decide(_geom(g), ctypes.c_int32(ks), _p(se), ctypes.c_int32(kt), _p(tf), ctypes.byref(D))
+    assert ok in (0, 1), ok
+    return int(D.value) if ok == 1 else None
+
+
 def transform(sector, row, pad, tim, theta, g=None):
     """S0: transformed (x, y, z) [n, 3] for clusters given by sector, row and raw coordinates."""
     n = len(pad)

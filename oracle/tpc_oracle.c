@@ -323,24 +323,22 @@ int or_select(int32_t n, int32_t n_rows, int32_t n_cand, const int32_t *cand_hit
  * sector of the same side with the integer constants (C30, S30), extrapolated linearly to the
  * row of the first hit of segment T, and compared there.  Mutual best pairs (smallest
  * (D, index)) are linked S -> T.  next[] receives the links. */
-static int merge_match(const or_geom *g, const int16_t *pad, const uint16_t *tim, const int32_t *bins,
-                       const int32_t *hs, int ns, const int32_t *ht, int64_t *D_out) {
+/* The merge decision on integer coordinates.  (X1, Y1, Z1) and (X2, Y2, Z2) are the hit MERGE_BACK
+ * positions before the outer end of S and its last hit, in the frame of S's sector ks; (XT, YT, ZT)
+ * is T's first hit in the frame of its sector kt.  Returns 1 and *D_out on a match. */
+static int merge_decide(const or_geom *g, int ks, int64_t X1, int64_t Y1, int64_t Z1, int64_t X2, int64_t Y2,
+                        int64_t Z2, int kt, int64_t XT, int64_t YT, int64_t ZT, int64_t *D_out) {
     int half = g->n_sectors / 2;
-    int ks = bins[hs[ns - 1]] / g->n_rows, kt = bins[ht[0]] / g->n_rows;
     int hs_ = ks % half, ht_ = kt % half;
     int sgn;
     if ((ks < half) != (kt < half)) return 0;
     if ((hs_ + 1) % half == ht_) sgn = +1;           /* T is the next sector in phi      */
     else if ((ht_ + 1) % half == hs_) sgn = -1;      /* T is the previous sector in phi  */
     else return 0;
-    int32_t hL = hs[ns - 1], hB = hs[ns - 1 - OR_MERGE_BACK];
-    int64_t X2 = g->xtab[bins[hL] % g->n_rows], Y2 = pad[hL], Z2 = tim[hL];
-    int64_t X1 = g->xtab[bins[hB] % g->n_rows], Y1 = pad[hB], Z1 = tim[hB];
     int64_t x2 = floor_shift(X2 * g->c30 + sgn * Y2 * g->s30, 30);
     int64_t y2 = floor_shift(-sgn * X2 * g->s30 + Y2 * g->c30, 30);
     int64_t x1 = floor_shift(X1 * g->c30 + sgn * Y1 * g->s30, 30);
     int64_t y1 = floor_shift(-sgn * X1 * g->s30 + Y1 * g->c30, 30);
-    int64_t XT = g->xtab[bins[ht[0]] % g->n_rows], YT = pad[ht[0]], ZT = tim[ht[0]];
     int64_t dxs = x2 - x1;
     if (dxs <= 0) return 0;
     if (iabs64(XT - x2) > OR_MERGE_XMAX) return 0;
@@ -350,6 +348,14 @@ static int merge_match(const or_geom *g, const int16_t *pad, const uint16_t *tim
     if (iabs64(dy) > OR_W_MERGE || iabs64(dz) > OR_W_MERGE) return 0;
     *D_out = dy * dy + dz * dz;
     return 1;
+}
+
+static int merge_match(const or_geom *g, const int16_t *pad, const uint16_t *tim, const int32_t *bins,
+                       const int32_t *hs, int ns, const int32_t *ht, int64_t *D_out) {
+    int ks = bins[hs[ns - 1]] / g->n_rows, kt = bins[ht[0]] / g->n_rows;
+    int32_t hL = hs[ns - 1], hB = hs[ns - 1 - OR_MERGE_BACK];
+    return merge_decide(g, ks, g->xtab[bins[hB] % g->n_rows], pad[hB], tim[hB], g->xtab[bins[hL] % g->n_rows],
+                        pad[hL], tim[hL], kt, g->xtab[bins[ht[0]] % g->n_rows], pad[ht[0]], tim[ht[0]], D_out);
 }
 
 int or_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
@@ -1013,4 +1019,14 @@ int or_propagate(const or_geom_in *gin, double x, const double *p, double xh, do
     if (!prop_step(&g, x, p, xh, pout, FF)) return 0;
     for (int i = 0; i < 5; i++) for (int j = 0; j < 5; j++) F[i * 5 + j] = FF[i][j];
     return 1;
+}
+
+/* S7 decision alone on integer end points (for the edge pins): 1 and *D on a match, else 0. */
+int or_merge_decide(const or_geom_in *gin, int32_t ks, const int64_t *s_end, int32_t kt, const int64_t *t_first,
+                    int64_t *D) {
+    or_geom g;
+    if (make_geom(gin, &g)) return -1;
+    *D = -1;
+    return merge_decide(&g, ks, s_end[0], s_end[1], s_end[2], s_end[3], s_end[4], s_end[5], kt, t_first[0],
+                        t_first[1], t_first[2], D);
 }
