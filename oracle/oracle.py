@@ -58,12 +58,18 @@ def _geom(g):
     return ctypes.byref(g if g is not None else geometry())
 
 
-def links(pad, tim, bin_off, g=None):
+# optional rules for inefficient data (bit flags; off by default)
+RULE_SKIP_ROW = 1       # a link may skip one row where the neighbouring row has no candidate
+RULE_GAP_MERGE = 2      # segments of one sector joined across a gap of pad rows
+
+
+def links(pad, tim, bin_off, g=None, rules=0):
     """S2 neighbour finding: (up, down) per cluster."""
     n = pad.shape[0]
     up = np.empty(n, np.int32)
     down = np.empty(n, np.int32)
-    rc = lib().or_links(_geom(g), _p(pad), _p(tim), _p(bin_off), ctypes.c_int32(n), _p(up), _p(down))
+    rc = lib().or_links_rules(_geom(g), _p(pad), _p(tim), _p(bin_off), ctypes.c_int32(n), ctypes.c_int32(rules),
+                              _p(up), _p(down))
     assert rc == 0, rc
     return up, down
 
@@ -113,13 +119,27 @@ def select(n_clusters, cand_hits, cand_n, cand_start, n_rows=159):
     return seg[:nc], segn[:nc], acc[:nc]
 
 
-def merge(pad, tim, bin_off, seg_hits, seg_n, g=None):
-    """S7 merge links: next[segment] or -1."""
+def merge(pad, tim, bin_off, seg_hits, seg_n, g=None, gap_next=None):
+    """S7 merge links: next[segment] or -1.  gap_next (gap links inside a sector, or None): segments
+    with a gap successor are no outer ends, segments with a gap predecessor no first segments."""
     nc = seg_n.shape[0]
     nxt = np.empty(max(nc, 1), np.int32)
     sh = np.ascontiguousarray(seg_hits, np.int32) if nc else np.zeros((1, 159), np.int32)
+    gn = np.ascontiguousarray(gap_next, np.int32) if gap_next is not None else None
     rc = lib().or_merge(_geom(g), _p(pad), _p(tim), _p(bin_off), ctypes.c_int32(pad.shape[0]),
-                        ctypes.c_int32(nc), _p(sh), _p(np.ascontiguousarray(seg_n, np.int32)), _p(nxt))
+                        ctypes.c_int32(nc), _p(sh), _p(np.ascontiguousarray(seg_n, np.int32)),
+                        _p(gn) if gn is not None else ctypes.c_void_p(0), _p(nxt))
+    assert rc == 0, rc
+    return nxt[:nc]
+
+
+def gap_merge(pad, tim, bin_off, seg_hits, seg_n, g=None):
+    """S7' gap links inside a sector: gap_next[segment] or -1."""
+    nc = seg_n.shape[0]
+    nxt = np.empty(max(nc, 1), np.int32)
+    sh = np.ascontiguousarray(seg_hits, np.int32) if nc else np.zeros((1, 159), np.int32)
+    rc = lib().or_gap_merge(_geom(g), _p(pad), _p(tim), _p(bin_off), ctypes.c_int32(pad.shape[0]),
+                            ctypes.c_int32(nc), _p(sh), _p(np.ascontiguousarray(seg_n, np.int32)), _p(nxt))
     assert rc == 0, rc
     return nxt[:nc]
 
@@ -140,23 +160,27 @@ def assemble(n_clusters, seg_hits, seg_n, nxt, n_rows=159):
     return off[:nt + 1].copy(), hits[:off[nt]].copy(), label[:n_clusters].copy()
 
 
-def track_event(pad, tim, bin_off, g=None, keep_stages=False):
-    """S2-S7 on one event; returns a dict with the final tracks (and every stage if asked)."""
+def track_event(pad, tim, bin_off, g=None, keep_stages=False, rules=0):
+    """S2-S7 on one event; returns a dict with the final tracks (and every stage if asked).  rules:
+    RULE_SKIP_ROW and / or RULE_GAP_MERGE (0: the plain readings)."""
     pad = np.ascontiguousarray(pad, np.int16)
     tim = np.ascontiguousarray(tim, np.uint16)
     bin_off = np.ascontiguousarray(bin_off, np.int32)
     n = pad.shape[0]
-    up, down = links(pad, tim, bin_off, g)
+    up, down = links(pad, tim, bin_off, g, rules)
     up2, down2 = clean(up, down)
     cst, cln = chains(up2, down2)
     ch, cn = follow(pad, tim, bin_off, cst, cln, up2, g)
     seg, segn, acc = select(n, ch, cn, cst)
-    nxt = merge(pad, tim, bin_off, seg, segn, g)
-    off, hits, label = assemble(n, seg, segn, nxt)
+    gap = gap_merge(pad, tim, bin_off, seg, segn, g) if rules & RULE_GAP_MERGE else None
+    nxt = merge(pad, tim, bin_off, seg, segn, g, gap_next=gap)
+    links_all = np.where(gap >= 0, gap, nxt).astype(np.int32) if gap is not None else nxt
+    off, hits, label = assemble(n, seg, segn, links_all)
     out = dict(trk_off=off, trk_hits=hits, label=label)
     if keep_stages:
         out.update(up=up, down=down, up2=up2, down2=down2, chain_start=cst, chain_len=cln,
-                   cand_hits=ch, cand_n=cn, seg_hits=seg, seg_n=segn, accepted=acc, next=nxt)
+                   cand_hits=ch, cand_n=cn, seg_hits=seg, seg_n=segn, accepted=acc, next=links_all,
+                   gap_next=gap if gap is not None else -np.ones_like(nxt))
     return out
 
 
@@ -288,6 +312,12 @@ def grad_fd(pad, tim, bin_off, trk_off, trk_hits, theta, h=(1e-6, 1e-4, 1e-4), g
                           _p(grad))
     assert rc == 0, rc
     return grad
+
+
+def rule_constants():
+    buf = np.zeros(8, np.int64)
+    k = lib().or_rule_constants(_p(buf), ctypes.c_int(8))
+    return dict(zip(["RULE_SKIP_ROW", "RULE_GAP_MERGE", "GAP_MAX"], buf[:k].tolist()))
 
 
 def constants():

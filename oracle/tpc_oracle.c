@@ -40,6 +40,12 @@
 #define OR_MERGE_BACK  3        /* direction baseline of a segment end, in hits               */
 #define OR_MAX_ROWS    512
 
+/* ---- optional rules for inefficient data (readings of the paper's CA on neighbouring rows and
+ *      of its segment merging; off by default) ------------------------------------------------ */
+#define OR_RULE_SKIP_ROW  1     /* a link may skip one row where row r+-1 has no candidate      */
+#define OR_RULE_GAP_MERGE 2     /* segments of one sector are joined across a gap of rows       */
+#define OR_GAP_MAX        24    /* largest row distance between the two ends of a gap link      */
+
 /* ---- reading constants (fit) ------------------------------------------------------------- */
 #define OR_SIGMA2      0.01     /* measurement variance of y and z (cm^2)                     */
 #define OR_SNP_MAX     0.999    /* |sin phi| limit of the local helix parametrisation          */
@@ -121,35 +127,56 @@ static int32_t lower_pad(const int16_t *pad, int32_t lo, int32_t hi, int64_t y) 
  * r-1 of the same sector that lie within the window |dY|, |dZ| <= W_LINK of c, the pair with the
  * smallest squared second difference D = (Yu+Yd-2Yc)^2 + (Zu+Zd-2Zc)^2 <= D_MAX; ties go to the
  * smaller (u, d).  The candidates are enumerated by scanning the pad-sorted bin; no grid.
+ *
+ * With OR_RULE_SKIP_ROW a side whose neighbouring row has no cluster inside the window looks one
+ * row further (rows r+-2) with the window doubled.  With the up partner a rows and the down
+ * partner b rows away, the straight-line residual is e = b Yu + a Yd - (a+b) Yc (and likewise in
+ * Z); its variance is k = a^2 + b^2 + (a+b)^2 times that of one coordinate, so the cut becomes
+ * 6 D <= k D_MAX (for a = b = 1 the rule above).  a and b are fixed per cluster, so the pairs of
+ * one cluster are still ranked by D.
  * ========================================================================================== */
-int or_links(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
-             int32_t n, int32_t *up, int32_t *down) {
+static int window_list(const int16_t *pad, const uint16_t *tim, const int32_t *bin_off, int b, int64_t yc,
+                       int64_t zc, int64_t w, int32_t *list) {
+    int m = 0;
+    for (int32_t u = lower_pad(pad, bin_off[b], bin_off[b + 1], yc - w); u < bin_off[b + 1] && pad[u] <= yc + w; u++)
+        if (iabs64((int64_t)tim[u] - zc) <= w) list[m++] = u;
+    return m;
+}
+
+int or_links_rules(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
+                   int32_t n, int32_t rules, int32_t *up, int32_t *down) {
     or_geom g;
     if (make_geom(gin, &g)) return -1;
     for (int32_t c = 0; c < n; c++) { up[c] = -1; down[c] = -1; }
     int32_t *ulist = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
     int32_t *dlist = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
+    const int skip = (rules & OR_RULE_SKIP_ROW) != 0;
     for (int s = 0; s < g.n_sectors; s++) {
         for (int r = 1; r < g.n_rows - 1; r++) {
             int b = s * g.n_rows + r;
-            int32_t u0 = bin_off[b + 1], u1 = bin_off[b + 2];
-            int32_t d0 = bin_off[b - 1], d1 = bin_off[b];
             for (int32_t c = bin_off[b]; c < bin_off[b + 1]; c++) {
                 int64_t yc = pad[c], zc = tim[c];
-                int nu = 0, nd = 0;
-                for (int32_t u = lower_pad(pad, u0, u1, yc - OR_W_LINK); u < u1 && pad[u] <= yc + OR_W_LINK; u++)
-                    if (iabs64((int64_t)tim[u] - zc) <= OR_W_LINK) ulist[nu++] = u;
-                for (int32_t d = lower_pad(pad, d0, d1, yc - OR_W_LINK); d < d1 && pad[d] <= yc + OR_W_LINK; d++)
-                    if (iabs64((int64_t)tim[d] - zc) <= OR_W_LINK) dlist[nd++] = d;
+                int64_t a = 1, bd_ = 1;
+                int nu = window_list(pad, tim, bin_off, b + 1, yc, zc, OR_W_LINK, ulist);
+                if (nu == 0 && skip && r + 2 <= g.n_rows - 1) {
+                    nu = window_list(pad, tim, bin_off, b + 2, yc, zc, 2 * OR_W_LINK, ulist);
+                    a = 2;
+                }
+                int nd = window_list(pad, tim, bin_off, b - 1, yc, zc, OR_W_LINK, dlist);
+                if (nd == 0 && skip && r - 2 >= 0) {
+                    nd = window_list(pad, tim, bin_off, b - 2, yc, zc, 2 * OR_W_LINK, dlist);
+                    bd_ = 2;
+                }
+                const int64_t k = a * a + bd_ * bd_ + (a + bd_) * (a + bd_);
                 int64_t bestD = -1;
                 int32_t bu = -1, bd = -1;
                 for (int i = 0; i < nu; i++) {
                     for (int j = 0; j < nd; j++) {
                         int32_t u = ulist[i], d = dlist[j];
-                        int64_t ey = (int64_t)pad[u] + pad[d] - 2 * yc;
-                        int64_t ez = (int64_t)tim[u] + tim[d] - 2 * zc;
+                        int64_t ey = bd_ * (int64_t)pad[u] + a * (int64_t)pad[d] - (a + bd_) * yc;
+                        int64_t ez = bd_ * (int64_t)tim[u] + a * (int64_t)tim[d] - (a + bd_) * zc;
                         int64_t D = ey * ey + ez * ez;
-                        if (D > OR_D_MAX) continue;
+                        if (6 * D > k * OR_D_MAX) continue;
                         if (bestD < 0 || D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
                             bestD = D; bu = u; bd = d;
                         }
@@ -163,6 +190,11 @@ int or_links(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, con
     free(ulist);
     free(dlist);
     return 0;
+}
+
+int or_links(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
+             int32_t n, int32_t *up, int32_t *down) {
+    return or_links_rules(gin, pad, tim, bin_off, n, 0, up, down);
 }
 
 /* S3  Link cleaning: keep a link only when it is mutual (both sides read the uncleaned links). */
@@ -196,7 +228,11 @@ int32_t or_chains(int32_t n, const int32_t *up2, const int32_t *down2, int32_t *
 /* ---- S5 helpers: integer steady-state Kalman filter (alpha-beta-gamma, Q16 fixed point) ---- */
 typedef struct { int64_t p, v, a; } abg;
 
-static void abg_init(abg *f, int64_t m0, int64_t m1) { f->p = m0 * 65536; f->v = (m1 - m0) * 65536; f->a = 0; }
+/* State at m0 with the velocity of the step to m1, drow >= 1 rows further: floor((m1 - m0) 2^16 /
+ * drow) per row (exact for drow = 1 or 2, a row skipped by a link). */
+static void abg_init(abg *f, int64_t m0, int64_t m1, int64_t drow) {
+    f->p = m0 * 65536; f->v = floor_div((m1 - m0) * 65536, drow); f->a = 0;
+}
 static void abg_predict(abg *f) { f->p += f->v + floor_shift(f->a, 1); f->v += f->a; }
 static void abg_update(abg *f, int64_t m) {
     int64_t e = m * 65536 - f->p;
@@ -221,14 +257,18 @@ static int32_t nearest(const int16_t *pad, const uint16_t *tim, const int32_t *b
 }
 
 /* Extend one direction: `hits` is the chain in filter order (first element farthest from the
- * extension side).  Appends found clusters to out[] in the order they are found. */
+ * extension side), rows[] their pad rows.  The filter steps once per pad row: a row that the chain
+ * skips (a link across an empty row) is a prediction without an update.  Appends found clusters
+ * to out[] in the order they are found. */
 static int follow_dir(const or_geom *g, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
-                      int sector, const int32_t *hits, int nh, int row_last, int dir, int32_t *out) {
+                      int sector, const int32_t *hits, const int *rows, int nh, int row_last, int dir,
+                      int32_t *out) {
     abg fy, fz;
-    abg_init(&fy, pad[hits[0]], pad[hits[1]]);
-    abg_init(&fz, tim[hits[0]], tim[hits[1]]);
+    int64_t d01 = iabs64(rows[1] - rows[0]);
+    abg_init(&fy, pad[hits[0]], pad[hits[1]], d01);
+    abg_init(&fz, tim[hits[0]], tim[hits[1]], d01);
     for (int k = 1; k < nh; k++) {
-        abg_predict(&fy); abg_predict(&fz);
+        for (int64_t j = iabs64(rows[k] - rows[k - 1]); j > 0; j--) { abg_predict(&fy); abg_predict(&fz); }
         abg_update(&fy, pad[hits[k]]); abg_update(&fz, tim[hits[k]]);
     }
     int nout = 0, misses = 0;
@@ -260,15 +300,17 @@ int or_follow(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, co
     int nbins = g.n_sectors * g.n_rows;
     int32_t *bins = cluster_bins(bin_off, nbins, n);
     int32_t chain[OR_MAX_ROWS], rev[OR_MAX_ROWS], ext_in[OR_MAX_ROWS], ext_out[OR_MAX_ROWS];
+    int crow[OR_MAX_ROWS], rrow[OR_MAX_ROWS];
     for (int32_t t = 0; t < n_chains; t++) {
         int nh = 0;
         for (int32_t x = chain_start[t]; x >= 0 && nh < OR_MAX_ROWS; x = up2[x]) chain[nh++] = x;
         if (nh != chain_len[t]) { free(bins); return -3; }
         int sector = bins[chain[0]] / g.n_rows;
-        int r_first = bins[chain[0]] % g.n_rows, r_last = bins[chain[nh - 1]] % g.n_rows;
-        int n_out = follow_dir(&g, pad, tim, bin_off, sector, chain, nh, r_last, +1, ext_out);
-        for (int k = 0; k < nh; k++) rev[k] = chain[nh - 1 - k];
-        int n_in = follow_dir(&g, pad, tim, bin_off, sector, rev, nh, r_first, -1, ext_in);
+        for (int k = 0; k < nh; k++) crow[k] = bins[chain[k]] % g.n_rows;
+        int r_first = crow[0], r_last = crow[nh - 1];
+        int n_out = follow_dir(&g, pad, tim, bin_off, sector, chain, crow, nh, r_last, +1, ext_out);
+        for (int k = 0; k < nh; k++) { rev[k] = chain[nh - 1 - k]; rrow[k] = crow[nh - 1 - k]; }
+        int n_in = follow_dir(&g, pad, tim, bin_off, sector, rev, rrow, nh, r_first, -1, ext_in);
         int32_t *o = cand_hits + (int64_t)t * g.n_rows;
         int m = 0;
         for (int k = n_in - 1; k >= 0; k--) o[m++] = ext_in[k];
@@ -359,9 +401,16 @@ static int merge_match(const or_geom *g, const int16_t *pad, const uint16_t *tim
 }
 
 int or_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
-             int32_t n, int32_t n_seg, const int32_t *seg_hits, const int32_t *seg_n, int32_t *next) {
+             int32_t n, int32_t n_seg, const int32_t *seg_hits, const int32_t *seg_n, const int32_t *gap_next,
+             int32_t *next) {
     or_geom g;
     if (make_geom(gin, &g)) return -1;
+    /* with gap links (OR_RULE_GAP_MERGE) a segment that continues in its own sector is not an outer
+     * end, and one that is continued from its own sector is not a first segment */
+    char *gap_src = (char *)calloc((size_t)n_seg + 1, 1), *gap_dst = (char *)calloc((size_t)n_seg + 1, 1);
+    if (gap_next)
+        for (int32_t i = 0; i < n_seg; i++)
+            if (gap_next[i] >= 0) { gap_src[i] = 1; gap_dst[gap_next[i]] = 1; }
     int nbins = g.n_sectors * g.n_rows;
     int32_t *bins = cluster_bins(bin_off, nbins, n);
     int64_t *bestT_D = (int64_t *)malloc(sizeof(int64_t) * (n_seg + 1));
@@ -382,7 +431,7 @@ int or_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, con
         sec_list[sec_cnt[k] + fill[k]++] = s;
     }
     for (int32_t s = 0; s < n_seg; s++) {
-        if (seg_n[s] < OR_N_MIN) continue;
+        if (seg_n[s] < OR_N_MIN || gap_src[s]) continue;
         const int32_t *hs = seg_hits + (int64_t)s * g.n_rows;
         int ks = bins[hs[0]] / g.n_rows, half = g.n_sectors / 2;
         int side0 = ks < half ? 0 : half;
@@ -391,7 +440,7 @@ int or_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, con
             for (int32_t i = sec_cnt[kt]; i < sec_cnt[kt + 1]; i++) {
                 int32_t t = sec_list[i];
                 int64_t D;
-                if (t == s) continue;
+                if (t == s || gap_dst[t]) continue;
                 if (!merge_match(&g, pad, tim, bins, hs, seg_n[s], seg_hits + (int64_t)t * g.n_rows, &D)) continue;
                 if (bestT[s] < 0 || D < bestT_D[s] || (D == bestT_D[s] && t < bestT[s])) { bestT[s] = t; bestT_D[s] = D; }
                 if (bestS[t] < 0 || D < bestS_D[t] || (D == bestS_D[t] && s < bestS[t])) { bestS[t] = s; bestS_D[t] = D; }
@@ -401,6 +450,110 @@ int or_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, con
     free(sec_cnt); free(sec_list); free(fill);
     for (int32_t s = 0; s < n_seg; s++)
         if (bestT[s] >= 0 && bestS[bestT[s]] == s) next[s] = bestT[s];
+    free(bestT_D); free(bestT); free(bestS_D); free(bestS); free(bins); free(gap_src); free(gap_dst);
+    return 0;
+}
+
+/* S7' Gap merge inside a sector (OR_RULE_GAP_MERGE; section 3, segment merging, applied to the
+ * segments of one sector that a gap of pad rows without clusters splits, e.g. dead rows).  The
+ * integer filter of the following runs over the kept hits of segment S in ascending rows (one
+ * step per row, an update per hit) and predicts on, row by row, up to OR_GAP_MAX rows past S's
+ * last hit.  A segment T of the same sector whose first kept hit lies on one of those rows, k rows
+ * past S's last hit, is a candidate when that hit is within the following's search radius after
+ * k-1 misses, W_F0 + W_F1 (k-1), of the prediction: D = dY^2 + dZ^2 <= radius^2.  Mutual best
+ * pairs by (D, index) are linked S -> T. */
+int or_gap_merge(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, const int32_t *bin_off,
+                 int32_t n, int32_t n_seg, const int32_t *seg_hits, const int32_t *seg_n, int32_t *gap_next) {
+    or_geom g;
+    if (make_geom(gin, &g)) return -1;
+    int nbins = g.n_sectors * g.n_rows;
+    int32_t *bins = cluster_bins(bin_off, nbins, n);
+    int64_t *bestT_D = (int64_t *)malloc(sizeof(int64_t) * (n_seg + 1));
+    int32_t *bestT = (int32_t *)malloc(sizeof(int32_t) * (n_seg + 1));
+    int64_t *bestS_D = (int64_t *)malloc(sizeof(int64_t) * (n_seg + 1));
+    int32_t *bestS = (int32_t *)malloc(sizeof(int32_t) * (n_seg + 1));
+    for (int32_t i = 0; i < n_seg; i++) { bestT[i] = -1; bestS[i] = -1; gap_next[i] = -1; }
+    /* accepted segments listed per bin of their first hit (sector, first row) */
+    int32_t *cnt = (int32_t *)calloc((size_t)nbins + 1, sizeof(int32_t));
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (n_seg + 1));
+    int32_t *fill = (int32_t *)calloc((size_t)nbins + 1, sizeof(int32_t));
+    for (int32_t t = 0; t < n_seg; t++)
+        if (seg_n[t] >= OR_N_MIN) cnt[bins[seg_hits[(int64_t)t * g.n_rows]] + 1]++;
+    for (int k = 0; k < nbins; k++) cnt[k + 1] += cnt[k];
+    for (int32_t t = 0; t < n_seg; t++) {
+        if (seg_n[t] < OR_N_MIN) continue;
+        int b = bins[seg_hits[(int64_t)t * g.n_rows]];
+        list[cnt[b] + fill[b]++] = t;
+    }
+    /* backward filter of every accepted segment: over its kept hits in descending rows, the state
+     * at its first hit */
+    abg *back_y = (abg *)malloc(sizeof(abg) * (n_seg + 1)), *back_z = (abg *)malloc(sizeof(abg) * (n_seg + 1));
+    for (int32_t t = 0; t < n_seg; t++) {
+        if (seg_n[t] < OR_N_MIN) continue;
+        const int32_t *ht = seg_hits + (int64_t)t * g.n_rows;
+        int nt_ = seg_n[t];
+        int64_t d = bins[ht[nt_ - 1]] % g.n_rows - bins[ht[nt_ - 2]] % g.n_rows;
+        abg_init(&back_y[t], pad[ht[nt_ - 1]], pad[ht[nt_ - 2]], d);
+        abg_init(&back_z[t], tim[ht[nt_ - 1]], tim[ht[nt_ - 2]], d);
+        for (int k = nt_ - 2; k >= 0; k--) {
+            for (int64_t j = bins[ht[k + 1]] % g.n_rows - bins[ht[k]] % g.n_rows; j > 0; j--) {
+                abg_predict(&back_y[t]); abg_predict(&back_z[t]);
+            }
+            abg_update(&back_y[t], pad[ht[k]]); abg_update(&back_z[t], tim[ht[k]]);
+        }
+    }
+    for (int32_t s = 0; s < n_seg; s++) {
+        if (seg_n[s] < OR_N_MIN) continue;
+        const int32_t *hs = seg_hits + (int64_t)s * g.n_rows;
+        int ns = seg_n[s];
+        int ks = bins[hs[0]] / g.n_rows;
+        abg fy, fz;
+        int64_t d01 = bins[hs[1]] % g.n_rows - bins[hs[0]] % g.n_rows;
+        abg_init(&fy, pad[hs[0]], pad[hs[1]], d01);
+        abg_init(&fz, tim[hs[0]], tim[hs[1]], d01);
+        for (int k = 1; k < ns; k++) {
+            for (int64_t j = bins[hs[k]] % g.n_rows - bins[hs[k - 1]] % g.n_rows; j > 0; j--) {
+                abg_predict(&fy); abg_predict(&fz);
+            }
+            abg_update(&fy, pad[hs[k]]); abg_update(&fz, tim[hs[k]]);
+        }
+        int rs = bins[hs[ns - 1]] % g.n_rows;
+        for (int rt = rs + 1; rt < g.n_rows && rt <= rs + OR_GAP_MAX; rt++) {
+            abg_predict(&fy); abg_predict(&fz);
+            int64_t py = q16_round(fy.p), pz = q16_round(fz.p);
+            /* the stop rules of the following: a prediction that leaves the sector, the drift range
+             * or the slope limit ends the search (the segment ended there, not in a gap) */
+            if (iabs64(py) > g.ymax[rt] || pz < 0 || pz > g.zmax || iabs64(fy.v) > (int64_t)OR_V_MAX * 65536) break;
+            if (rt - rs - 1 < OR_M_MISS) continue;      /* a shorter gap the following bridges */
+            int64_t w = OR_W_F0 + (int64_t)OR_W_F1 * (rt - rs - 1);
+            int b = ks * g.n_rows + rt;
+            for (int32_t i = cnt[b]; i < cnt[b + 1]; i++) {
+                int32_t t = list[i];
+                if (t == s) continue;
+                int32_t h = seg_hits[(int64_t)t * g.n_rows];
+                int64_t dy = pad[h] - py, dz = tim[h] - pz;
+                if (iabs64(dy) > w || iabs64(dz) > w || dy * dy + dz * dz > w * w) continue;
+                /* and T's backward prediction at S's last row, rt - rs rows back */
+                abg by = back_y[t], bz = back_z[t];
+                int inside = 1;
+                for (int j = 1; j <= rt - rs && inside; j++) {
+                    abg_predict(&by); abg_predict(&bz);
+                    int64_t qy = q16_round(by.p), qz = q16_round(bz.p);
+                    inside = iabs64(qy) <= g.ymax[rt - j] && qz >= 0 && qz <= g.zmax &&
+                             iabs64(by.v) <= (int64_t)OR_V_MAX * 65536;
+                }
+                if (!inside) continue;
+                int64_t ey = pad[hs[ns - 1]] - q16_round(by.p), ez = tim[hs[ns - 1]] - q16_round(bz.p);
+                if (iabs64(ey) > w || iabs64(ez) > w || ey * ey + ez * ez > w * w) continue;
+                int64_t D = dy * dy + dz * dz + ey * ey + ez * ez;
+                if (bestT[s] < 0 || D < bestT_D[s] || (D == bestT_D[s] && t < bestT[s])) { bestT[s] = t; bestT_D[s] = D; }
+                if (bestS[t] < 0 || D < bestS_D[t] || (D == bestS_D[t] && s < bestS[t])) { bestS[t] = s; bestS_D[t] = D; }
+            }
+        }
+    }
+    for (int32_t s = 0; s < n_seg; s++)
+        if (bestT[s] >= 0 && bestS[bestT[s]] == s) gap_next[s] = bestT[s];
+    free(cnt); free(list); free(fill); free(back_y); free(back_z);
     free(bestT_D); free(bestT); free(bestS_D); free(bestS); free(bins);
     return 0;
 }
@@ -960,6 +1113,13 @@ int or_grad_fd(const or_geom_in *gin, const int16_t *pad, const uint16_t *tim, c
 }
 
 /* Reading constants, exported so that a test can compare them with the CUDA library's. */
+int or_rule_constants(int64_t *out, int cap) {
+    const int64_t v[] = {OR_RULE_SKIP_ROW, OR_RULE_GAP_MERGE, OR_GAP_MAX};
+    int n = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < n && i < cap; i++) out[i] = v[i];
+    return n;
+}
+
 int or_constants(int64_t *out, int cap) {
     int64_t v[] = {OR_W_LINK, OR_D_MAX, OR_N_SEED, OR_M_MISS, OR_W_F0, OR_W_F1, OR_V_MAX, OR_N_MIN,
                    OR_W_MERGE, OR_MERGE_XMAX, OR_MERGE_BACK};

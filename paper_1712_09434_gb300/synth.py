@@ -62,6 +62,11 @@ class EventConfig:
     seed: int = 0
     smear: float = 0.1
     theta: np.ndarray | None = None      # injected calibration [s_vd, d_0..35, a_0..35]
+    # cluster inefficiency: rows without any cluster in every sector (inclusive ranges), and the
+    # probability that a track crossing gives no cluster (drawn from a separate seeded stream, so
+    # that the other draws of the event do not change)
+    dead_rows: tuple = ()
+    drop_frac: float = 0.0
 
 
 @dataclasses.dataclass
@@ -265,6 +270,16 @@ def make_event(cfg: EventConfig) -> Event:
     y_m, d_m, sig_true = y_m[inside], d_m[inside], sig_true[inside]
     ns = sig_trk.size
 
+    if cfg.drop_frac > 0 or cfg.dead_rows:
+        keep = np.ones(ns, bool)
+        if cfg.drop_frac > 0:
+            keep &= np.random.default_rng([cfg.seed, 0x1eaf]).random(ns) >= cfg.drop_frac
+        for r0, r1 in cfg.dead_rows:
+            keep &= (sig_row < r0) | (sig_row > r1)
+        sig_trk, sig_sec, sig_row = sig_trk[keep], sig_sec[keep], sig_row[keep]
+        y_m, d_m, sig_true = y_m[keep], d_m[keep], sig_true[keep]
+        ns = sig_trk.size
+
     n_noise = int(round(cfg.noise_frac * ns))
     if cfg.single_sector:
         nz_sec = np.zeros(n_noise, np.int64)
@@ -274,6 +289,12 @@ def make_event(cfg: EventConfig) -> Event:
     ymax = ROW_X[nz_row] * TAN_HALF
     nz_y = rng.uniform(-1.0, 1.0, size=n_noise) * ymax
     nz_d = rng.uniform(0.0, Z_MAX, size=n_noise)
+    if cfg.dead_rows:
+        alive = np.ones(n_noise, bool)
+        for r0, r1 in cfg.dead_rows:
+            alive &= (nz_row < r0) | (nz_row > r1)
+        nz_sec, nz_row, nz_y, nz_d = nz_sec[alive], nz_row[alive], nz_y[alive], nz_d[alive]
+        n_noise = int(alive.sum())
 
     sec = np.concatenate([sig_sec, nz_sec]).astype(np.int64)
     row = np.concatenate([sig_row, nz_row]).astype(np.int64)
@@ -313,6 +334,15 @@ def full_event(seed=1002, n_tracks=5000):
 def central_event(seed=1003, n_tracks=20000):
     """Central-Pb-Pb-shaped event: 20,000 tracks incl. 10 % low-pT loopers, 30 % noise."""
     return EventConfig(n_tracks=n_tracks, noise_frac=0.30, looper_frac=0.10, seed=seed)
+
+
+def inefficient_central(seed=1006, n_tracks=20000):
+    """The central-shaped event with cluster inefficiency: 5 % of the track crossings give no
+    cluster (single-row gaps) and two ranges of dead pad rows in every sector, rows 60-61 (a gap
+    the following bridges, the neighbour finding does not) and rows 100-111 (twelve rows, more than
+    the following bridges)."""
+    return EventConfig(n_tracks=n_tracks, noise_frac=0.30, looper_frac=0.10, seed=seed,
+                       dead_rows=((60, 61), (100, 111)), drop_frac=0.05)
 
 
 def batch_configs(n_events=64, seed0=2000):
@@ -494,3 +524,35 @@ def time_frame(events, per_drift=5.0, slice_len=DRIFT_LSB, seed=3000, t0=None) -
     ev_off = bin_off[::nb].astype(np.int64)
     return TimeFrame(pad_fp=pad.astype(np.int16), time_fp=loc.astype(np.uint16), bin_off=bin_off.astype(np.int32),
                      ev_off=ev_off, slice_len=int(slice_len), t0=t0, mc=mc, collisions=list(events))
+
+
+def track_quality(ev: Event, trk_off, trk_hits, min_pt=0.3, min_hits=30, purity=0.9, coverage=0.8):
+    """Truth matching of reconstructed tracks (a sanity figure; the paper prints none for these
+    events).  A generating particle with pT > min_pt and at least min_hits clusters, not a looper
+    (pT > 0.15 GeV), is found whole when one track holds at least `coverage` of its clusters and
+    at least `purity` of that track's hits are its clusters.  Returns (efficiency, particles, fake
+    fraction of tracks below `purity`)."""
+    trk_off = np.asarray(trk_off)
+    trk_hits = np.asarray(trk_hits)
+    nt = trk_off.shape[0] - 1
+    n_of = np.bincount(ev.mc_track[ev.mc_track >= 0], minlength=len(ev.trk_pt))
+    want = (ev.trk_pt > max(min_pt, 0.15)) & (n_of >= min_hits)
+    found = np.zeros(len(ev.trk_pt), bool)
+    fakes = 0
+    for t in range(nt):
+        lab = ev.mc_track[trk_hits[trk_off[t]:trk_off[t + 1]]]
+        n = lab.size
+        lab = lab[lab >= 0]
+        if lab.size == 0:
+            fakes += 1
+            continue
+        vals, cnt = np.unique(lab, return_counts=True)
+        k = int(np.argmax(cnt))
+        p, c = int(vals[k]), int(cnt[k])
+        if c < purity * n:
+            fakes += 1
+            continue
+        if c >= coverage * n_of[p]:
+            found[p] = True
+    n_want = int(want.sum())
+    return float(found[want].sum() / max(n_want, 1)), n_want, fakes / max(nt, 1)

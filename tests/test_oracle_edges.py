@@ -14,6 +14,10 @@ dropped stop condition or a wrong tie-break fails here:
   R-10 assembly: a cycle of merge links is cut in front of its smallest segment.
   R-6 / R-7 cleaning and chains: every mutual link is kept and every start of a chain of at least
       five hits gives a chain (brute force on tiny sectors).
+  R-5' / R-7' / R-9' (rules for inefficient data, off by default): links across one empty row with
+      the window doubled and the cut scaled by the row distances; the following's filter steps
+      once per row across a skipped row; the gap merge inside a sector (gaps of 8 to 23 empty
+      rows, the following's radius, both extrapolations, the stop rules, mutual best).
 """
 import math
 
@@ -324,3 +328,228 @@ def test_cleaning_keeps_every_mutual_link_and_chains_are_complete():
         assert list(zip(st.tolist(), ln.tolist())) == want
         n_chain_total += len(want)
     assert n_chain_total > 30
+
+
+# ---------------------------------------------------------------------------------------------
+# Rules for inefficient data (off by default): links across one empty row, gap merge in a sector
+# ---------------------------------------------------------------------------------------------
+
+def _brute_links_skip(pad, tim, bin_off, n_rows, n_sectors, W=384, DMAX=13600):
+    """Naive enumeration of the skip-row rule: a side whose neighbouring row has no cluster in the
+    window takes the row after it with the window doubled; residual b*u + a*d - (a+b)*c with
+    a, b the row distances; cut 6 D <= (a^2 + b^2 + (a+b)^2) D_MAX; minimum (D, u, d)."""
+    n = len(pad)
+    up = -np.ones(n, np.int32)
+    down = -np.ones(n, np.int32)
+    P, T = pad.astype(np.int64), tim.astype(np.int64)
+
+    def cands(b, c, w):
+        return [x for x in range(bin_off[b], bin_off[b + 1]) if abs(P[x] - P[c]) <= w and abs(T[x] - T[c]) <= w]
+
+    for s in range(n_sectors):
+        for r in range(1, n_rows - 1):
+            b = s * n_rows + r
+            for c in range(bin_off[b], bin_off[b + 1]):
+                us, a = cands(b + 1, c, W), 1
+                if not us and r + 2 <= n_rows - 1:
+                    us, a = cands(b + 2, c, 2 * W), 2
+                ds, bb = cands(b - 1, c, W), 1
+                if not ds and r - 2 >= 0:
+                    ds, bb = cands(b - 2, c, 2 * W), 2
+                k = a * a + bb * bb + (a + bb) ** 2
+                best = None
+                for u in us:
+                    for d in ds:
+                        D = (bb * P[u] + a * P[d] - (a + bb) * P[c]) ** 2 + (bb * T[u] + a * T[d] - (a + bb) * T[c]) ** 2
+                        if 6 * D <= k * DMAX and (best is None or (D, u, d) < best):
+                            best = (D, u, d)
+                if best is not None:
+                    up[c], down[c] = best[1], best[2]
+    return up, down
+
+
+def _tiny_sparse_event(rng, n_rows=10, n_sectors=2, max_per_row=3, empty=0.35):
+    pads, tims, bins = [], [], []
+    for s in range(n_sectors):
+        for r in range(n_rows):
+            k = 0 if rng.random() < empty else int(rng.integers(1, max_per_row + 1))
+            y = rng.integers(-500, 501, k)
+            z = 8000 + rng.integers(-500, 501, k)
+            o = np.lexsort((z, y))
+            pads.append(y[o]); tims.append(z[o]); bins.append(np.full(k, s * n_rows + r))
+    b = np.concatenate(bins)
+    return (np.concatenate(pads).astype(np.int16), np.concatenate(tims).astype(np.uint16),
+            np.searchsorted(b, np.arange(n_sectors * n_rows + 1)).astype(np.int32))
+
+
+def test_skip_row_links_match_brute_force_on_tiny_sectors():
+    """R-5 with the skip-row rule against a naive enumeration, on tiny sectors with many empty
+    rows and windows (so that both a = 2 and b = 2 occur)."""
+    rng = np.random.default_rng(300)
+    g = O.geometry(n_sectors=2, n_rows=10)
+    n_skip = 0
+    for trial in range(60):
+        pad, tim, bin_off = _tiny_sparse_event(rng)
+        up, down = O.links(pad, tim, bin_off, g, rules=O.RULE_SKIP_ROW)
+        bu, bd = _brute_links_skip(pad, tim, bin_off, 10, 2)
+        np.testing.assert_array_equal(up, bu)
+        np.testing.assert_array_equal(down, bd)
+        rows = np.repeat(np.arange(20) % 10, np.diff(bin_off))
+        has = up >= 0
+        n_skip += int((np.abs(rows[up[has]] - rows[has]) == 2).sum() + (np.abs(rows[down[has]] - rows[has]) == 2).sum())
+        # without the rule only links to the neighbouring rows (the plain reading)
+        u0, _ = O.links(pad, tim, bin_off, g)
+        assert np.all((u0 < 0) | (np.abs(rows[np.maximum(u0, 0)] - rows) == 1))
+    assert n_skip > 20
+
+
+@pytest.mark.parametrize("a,b,limit", [(2, 1, 178), (1, 2, 178), (2, 2, 116)])
+def test_skip_row_cut_scales_with_the_row_distance(a, b, limit):
+    """A straight line with the row(s) next to c removed: the partner across the empty row links at
+    displacements up to the scaled cut and not one LSB beyond.  (a, b) = (2, 1): k = 14, 6 D <=
+    14 * 13600 allows a residual of 178 (31684) and not 179 (32041); with the displacement on the
+    partner two rows away the residual is b * delta.  (2, 2): k = 24, residual 2 * delta, 232 (delta =
+    116) passes and 234 (117) does not."""
+    g = O.geometry(n_sectors=1, n_rows=7)
+    y = lambda r: 100 + 30 * r
+    z = lambda r: 9000 + 20 * r
+    for delta, ok in [(limit, True), (limit + 1, False)]:
+        # c on row 3; the up partner a rows up, the down partner b rows down; the displacement sits
+        # on the partner across the empty row (on the up partner when both sides skip)
+        pts = {3: (y(3), z(3))}
+        pts[3 + a] = (y(3 + a) + (delta if a == 2 else 0), z(3 + a))
+        pts[3 - b] = (y(3 - b) + (delta if (b == 2 and a == 1) else 0), z(3 - b))
+        rows = sorted(pts)
+        pad = np.array([pts[r][0] for r in rows], np.int16)
+        tim = np.array([pts[r][1] for r in rows], np.uint16)
+        bin_off = np.searchsorted(np.array(rows), np.arange(8)).astype(np.int32)
+        up, down = O.links(pad, tim, bin_off, g, rules=O.RULE_SKIP_ROW)
+        c = rows.index(3)
+        assert (up[c] >= 0) == ok, (a, b, delta, up[c], down[c])
+        u0, _ = O.links(pad, tim, bin_off, g)
+        assert u0[c] == -1                      # the plain reading never links across the gap
+
+
+def test_following_steps_one_row_per_predict_across_a_skipped_row():
+    """R-7 with a chain that skips a row: the filter predicts twice across the skip (a single
+    prediction would double the slope), so the extension finds every cluster of the line."""
+    b = Builder()
+    rows = [20, 21, 23, 24, 26, 27, 28, 29]          # rows 22 and 25 skipped inside the chain
+    chain = [b.add(0, r, -300 + 40 * r, 5000 + 25 * r) for r in rows]
+    beyond = b.line(0, range(30, 80), -300, 40, 5000, 25)
+    below = b.line(0, range(5, 20), -300, 40, 5000, 25)
+    cand, index = _follow(b, chain)
+    assert {index[p] for p in beyond} <= cand
+    assert {index[p] for p in below} <= cand
+
+
+def _gap_segments(builder, segs):
+    """Segments (lists of points, ascending rows) as the selection's kept-hit arrays."""
+    pad, tim, bin_off, index = builder.build()
+    seg = -np.ones((len(segs), 159), np.int32)
+    for k, pts in enumerate(segs):
+        seg[k, :len(pts)] = [index[p] for p in pts]
+    return pad, tim, bin_off, seg, np.array([len(p) for p in segs], np.int32)
+
+
+@pytest.mark.parametrize("gap", [7, 8, 12, 24, 25])
+def test_gap_merge_joins_a_straight_track_across_dead_rows(gap):
+    """R-9' (gap merge): two pieces of one straight track separated by `gap` empty rows are joined
+    when at least 8 rows are empty (fewer are the following's to bridge) and the second piece starts
+    at most 24 rows past the first piece's end."""
+    b = Builder()
+    s1 = b.line(3, range(30, 60), -300, 9, 7000, 30)
+    s2 = b.line(3, range(60 + gap, min(60 + gap + 30, 159)), -300, 9, 7000, 30)
+    pad, tim, bin_off, seg, segn = _gap_segments(b, [s1, s2])
+    nxt = O.gap_merge(pad, tim, bin_off, seg, segn)
+    rt_minus_rs = gap + 1
+    assert (nxt[0] == 1) == (8 <= gap and rt_minus_rs <= 24), (gap, nxt)
+    assert nxt[1] == -1
+
+
+@pytest.mark.parametrize("gap", [8, 12, 20])
+def test_gap_merge_window_is_the_radius_after_the_missed_rows(gap):
+    """The second piece shifted parallel by delta in Y: both the forward prediction of the first
+    piece and the backward prediction of the second are off by delta, so the link holds iff delta <=
+    77 + 38 (k - 1) with k the row distance between the two ends."""
+    w = 77 + 38 * gap
+    for delta, ok in [(w, True), (w + 1, False), (-w, True), (-w - 1, False)]:
+        b = Builder()
+        s1 = b.line(4, range(30, 60), -300, 9, 7000, 30)
+        s2 = [b.add(4, r, -300 + 9 * r + delta, 7000 + 30 * r) for r in range(60 + gap, 60 + gap + 30)]
+        pad, tim, bin_off, seg, segn = _gap_segments(b, [s1, s2])
+        nxt = O.gap_merge(pad, tim, bin_off, seg, segn)
+        assert (nxt[0] == 1) == ok, (gap, delta)
+
+
+def test_gap_merge_stops_where_the_track_leaves_the_sector():
+    """A piece whose extrapolation leaves the sector acceptance inside the gap is not joined to a
+    piece that starts further on at the extrapolated position (it left the sector there)."""
+    R0, gap = 60, 12
+    slope = 90
+    b = Builder()
+    # ends at row 59 about 10 rows before it would cross |y| = ymax
+    y_end = ymax(R0 + 6) - 6 * slope
+    s1 = [b.add(5, r, y_end - slope * (R0 - 1 - r), 7000 + 30 * r) for r in range(R0 - 30, R0)]
+    s2 = [b.add(5, r, min(y_end + slope * (r - R0 + 1), ymax(r)), 7000 + 30 * r) for r in range(R0 + gap, R0 + gap + 20)]
+    pad, tim, bin_off, seg, segn = _gap_segments(b, [s1, s2])
+    assert O.gap_merge(pad, tim, bin_off, seg, segn)[0] == -1
+
+
+def test_gap_merge_takes_the_mutual_best_pair():
+    """Two candidate second pieces: the nearer one to the extrapolation is linked, the other not."""
+    b = Builder()
+    s1 = b.line(6, range(30, 60), -300, 9, 7000, 30)
+    near = [b.add(6, r, -300 + 9 * r + 40, 7000 + 30 * r) for r in range(72, 100)]
+    far = [b.add(6, r, -300 + 9 * r - 200, 7000 + 30 * r) for r in range(72, 100)]
+    pad, tim, bin_off, seg, segn = _gap_segments(b, [s1, far, near])
+    nxt = O.gap_merge(pad, tim, bin_off, seg, segn)
+    assert nxt[0] == 2 and nxt[1] == -1 and nxt[2] == -1
+
+
+def test_rules_leave_an_efficient_event_nearly_unchanged_and_help_an_inefficient_one():
+    """Sanity of the readings (the paper prints no efficiency): with the rules the found-whole
+    efficiency of an event with dead rows rises well above the plain tracking's, and on the same
+    event shape without inefficiency it does not drop."""
+    from paper_1712_09434_gb300 import synth
+    ev = synth.make_event(synth.inefficient_central(n_tracks=3000))
+    e0 = synth.track_quality(ev, *(lambda r: (r["trk_off"], r["trk_hits"]))(O.track_event(ev.pad_fp, ev.time_fp, ev.bin_off)))
+    e3 = synth.track_quality(ev, *(lambda r: (r["trk_off"], r["trk_hits"]))(O.track_event(ev.pad_fp, ev.time_fp, ev.bin_off, rules=3)))
+    assert e3[0] > e0[0] + 0.3, (e0, e3)
+    cfg = synth.central_event(n_tracks=3000)
+    ef = synth.make_event(cfg)
+    f0 = synth.track_quality(ef, *(lambda r: (r["trk_off"], r["trk_hits"]))(O.track_event(ef.pad_fp, ef.time_fp, ef.bin_off)))
+    f3 = synth.track_quality(ef, *(lambda r: (r["trk_off"], r["trk_hits"]))(O.track_event(ef.pad_fp, ef.time_fp, ef.bin_off, rules=3)))
+    assert f3[0] > f0[0] - 0.01, (f0, f3)
+
+
+def test_following_skip_keeps_the_prediction_exact():
+    """A steep line (150 LSB per row) whose chain skips the row before its last hit: stepping the
+    filter once per row keeps the prediction at the first extension row exact, so the line's
+    cluster there (distance 0) wins over a decoy 54 LSB below it; a single prediction across the
+    skip would put the prediction on the decoy."""
+    b = Builder()
+    rows = [20, 21, 22, 23, 24, 25, 26, 27, 29]
+    chain = [b.add(0, r, -2500 + 150 * r, 6000 + 10 * r) for r in rows]
+    true30 = b.add(0, 30, -2500 + 150 * 30, 6300)
+    decoy = b.add(0, 30, -2500 + 150 * 30 - 54, 6300)
+    cand, index = _follow(b, chain)
+    assert index[true30] in cand and index[decoy] not in cand
+
+
+def test_gap_merge_needs_both_extrapolations():
+    """The second piece starts on the first piece's extrapolation but runs at a slope 60 LSB per row
+    steeper: its own extrapolation back to the first piece's end misses by 60 x 13 = 780 > 533 (the
+    radius after 12 empty rows), so the pieces are not joined."""
+    b = Builder()
+    s1 = b.line(7, range(30, 60), -300, 9, 7000, 30)
+    y72 = -300 + 9 * 72
+    s2 = [b.add(7, r, y72 + 69 * (r - 72), 7000 + 30 * r) for r in range(72, 100)]
+    pad, tim, bin_off, seg, segn = _gap_segments(b, [s1, s2])
+    assert O.gap_merge(pad, tim, bin_off, seg, segn)[0] == -1
+    # the same piece continuing the first one's slope is joined
+    b = Builder()
+    s1 = b.line(7, range(30, 60), -300, 9, 7000, 30)
+    s2 = b.line(7, range(72, 100), -300, 9, 7000, 30)
+    pad, tim, bin_off, seg, segn = _gap_segments(b, [s1, s2])
+    assert O.gap_merge(pad, tim, bin_off, seg, segn)[0] == 1
