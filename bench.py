@@ -34,9 +34,17 @@ sys.path.insert(0, ROOT)
 from paper_1712_09434_gb300 import synth  # noqa: E402
 
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
-# kernels of one step: tracking graph (grid 1, links 1, chains 8, follow 1, select 1, merge 17,
-# refit 1) + refit_grad (cluster bins 1, pack 1, length sort 3, forward and reverse pass 2, reduce 2)
-LAUNCHES_PER_STEP = 43
+# kernels of one step: tracking graph (bin offset check 2, grid 1, links 1, chains 8, follow 1,
+# select 1, merge 17, refit 1) + refit_grad (bin offset check 2, cluster bins 1, pack 1, length
+# sort 3, forward and reverse pass 2, reduce 2; the stored-state form adds the chunk lengths and
+# their scan, 4)
+LAUNCHES_TRACKING = 32
+LAUNCHES_REFIT_GRAD = {"checkpoints": 11, "stored states": 15}
+
+
+def launches_per_step(tuning_best):
+    form = "stored states" if tuning_best and tuple(tuning_best.get("refit_grad", (0, 0, 0)))[2] == 1 else "checkpoints"
+    return LAUNCHES_TRACKING + LAUNCHES_REFIT_GRAD[form], form
 WORKLOAD = "batch-64-events-logU-100-20000-tracks-20pct-noise"
 
 
@@ -154,6 +162,40 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def fp32_peak(seconds=1.0):
+    """Measured FP32 FMA throughput of this GPU (tpc_fma_peak): 4 CTAs of 256 threads per SM,
+    8 independent FMA chains per thread, one launch of ~`seconds` timed with CUDA events (median of
+    three) while nvidia-smi samples the SM clock.  The roof of the Kalman refit and its adjoint."""
+    import torch
+    from paper_1712_09434_gb300 import capi
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ctas, threads = 4, 256
+    out = torch.empty(sms * ctas * threads, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(iters):
+        e0.record()
+        fl = capi.tpc_fma_peak(out, iters, ctas, threads)
+        e1.record()
+        e1.synchronize()
+        return fl, e0.elapsed_time(e1) * 1e-3
+
+    run(1000)
+    fl, t = run(20000)
+    iters = max(1000, int(20000 * seconds / max(t, 1e-6)))
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    rates = []
+    for _ in range(3):
+        fl, t = run(iters)
+        rates.append(fl / t / 1e12)
+    clk = clocks.stop()
+    return {"tflops": float(np.median(rates)), "runs": [float(r) for r in rates], "seconds_per_run": t,
+            "config": "%d SMs x %d CTAs x %d threads, 8 FMA chains per thread" % (sms, ctas, threads),
+            "clocks": clk}
+
+
 def shard_seed0(rank):
     """First event seed of a rank: weak scaling, every rank tracks its own batch of events with no
     data exchange (events are independent; the seeds of two ranks never overlap for <= 1000 events)."""
@@ -185,7 +227,7 @@ def run_native(args, rank, world):
     n_clusters = int(d["pad"].shape[0])
     n_ev = args.events
     cl = capi.Clusters.from_numpy(d["pad"], d["tim"], d["bin_off"], n_ev)
-    cap_t = n_clusters // 8 + 1024
+    cap_t = n_clusters // 10 + 1024        # a track has at least 10 hits
     ctx = capi.Context(max_clusters=n_clusters, max_events=n_ev)
     tr = capi.Tracks(n_clusters, n_ev, cap_t, n_clusters)
     theta = torch.tensor(synth.theta_nominal(), dtype=torch.float64, device=dev)
@@ -205,9 +247,8 @@ def run_native(args, rank, world):
 
     w_batch = select(tr, int(tr.n_tracks.item()))
 
-    def step():
-        ctx.tpc_track_batch(cl, tr)
-        ctx.tpc_refit_grad(cl, tr, theta, s_chi2, grad, w_batch)
+    def step():       # tracking + refit / adjoint of the tracks: one CUDA graph launch
+        ctx.tpc_track_refit_batch(cl, tr, theta, s_chi2, grad, w_batch)
 
     # launch shapes: autotuned on this workload (outside the timed region), or from the cache
     from paper_1712_09434_gb300 import tune
@@ -274,8 +315,7 @@ def run_native(args, rank, world):
             st_.wait_event(e_start)
         for k in range(k_steps):
             c_, cl_, tr_, sc_, gr_, st_ = lanes[k % 2]
-            c_.tpc_track_batch(cl_, tr_, stream=st_)
-            c_.tpc_refit_grad(cl_, tr_, theta, sc_, gr_, w_batch, stream=st_)
+            c_.tpc_track_refit_batch(cl_, tr_, theta, sc_, gr_, w_batch, stream=st_)
         for c_, cl_, tr_, sc_, gr_, st_ in lanes:
             stream.wait_stream(st_)
 
@@ -318,36 +358,45 @@ def run_native(args, rank, world):
            "n_hits": n_hits, "clocks": clk, "tuning": tuning_info, "prof": prof}
     if args.only_step:
         return out
+    # the measured FP32 roof of the Kalman stages (seconds-long FMA loop, clocks sampled)
+    out["fp32_peak"] = fp32_peak()
 
-    # end to end through the binding with host (pinned) buffers
+    # end to end through the binding with host (pinned) buffers: every step copies its inputs in
+    # and the whole result set out (all outputs of tpc_track_batch, sum of chi2 and gradient)
     h_pad = torch.from_numpy(d["pad"]).pin_memory()
     h_tim = torch.from_numpy(d["tim"].view(np.int16)).pin_memory()
     h_bo = torch.from_numpy(d["bin_off"]).pin_memory()
-    h_label = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
-    h_off = torch.empty(cap_t + 1, dtype=torch.int32).pin_memory()
-    h_hits = torch.empty(n_clusters, dtype=torch.int32).pin_memory()
-    h_par = torch.empty(cap_t * 5, dtype=torch.float32).pin_memory()
-    h_red = torch.empty(74, dtype=torch.float64).pin_memory()
     d_pad, d_tim, d_bo = cl.pad_fp, cl.time_fp, cl.bin_off
+
+    def out_views(t_):
+        return (t_.label[:n_clusters], t_.trk_off[:cap_t + 1], t_.trk_hits[:n_clusters], t_.ev_trk_off[:n_ev + 1],
+                t_.par[:cap_t * 5], t_.xref[:cap_t], t_.cov[:cap_t * 15], t_.chi2[:cap_t], t_.ndf[:cap_t],
+                t_.n_tracks[:1])
+
+    def host_set():
+        return tuple(torch.empty_like(x, device="cpu").pin_memory() for x in out_views(tr)) + \
+            (torch.empty(74, dtype=torch.float64).pin_memory(),)
+
+    h_seq = host_set()
 
     def e2e():
         d_pad.copy_(h_pad, non_blocking=True)
         d_tim.copy_(h_tim, non_blocking=True)
         d_bo.copy_(h_bo, non_blocking=True)
         step()
-        h_label.copy_(tr.label[:n_clusters], non_blocking=True)
-        h_off.copy_(tr.trk_off[:cap_t + 1], non_blocking=True)
-        h_hits.copy_(tr.trk_hits[:n_clusters], non_blocking=True)
-        h_par.copy_(tr.par[:cap_t * 5], non_blocking=True)
-        h_red[:1].copy_(s_chi2, non_blocking=True)
-        h_red[1:].copy_(grad, non_blocking=True)
+        for dst, src in zip(h_seq, out_views(tr)):
+            dst.copy_(src, non_blocking=True)
+        h_seq[-1][:1].copy_(s_chi2, non_blocking=True)
+        h_seq[-1][1:].copy_(grad, non_blocking=True)
 
     if world > 1:
         torch.distributed.barrier()
     ms_e2e_seq, _ = timed(e2e, max(1, min(args.steps, 5)), 1)
     ms_e2e_seq, _ = aggregate(ms_e2e_seq, n_clusters, world, dev)
     h2d = h_pad.numel() * 2 + h_tim.numel() * 2 + h_bo.numel() * 4
-    d2h = (h_label.numel() + h_off.numel() + h_hits.numel()) * 4 + h_par.numel() * 4 + h_red.numel() * 8
+    d2h = sum(x.numel() * x.element_size() for x in h_seq)
+    # the device-resident result of this step, for the check of every host copy below
+    ref_red = torch.cat([s_chi2, grad]).cpu()
 
     # pipelined: the two contexts of the timed steps take the steps in turn, each on its own compute
     # stream.  Every context has two input buffer sets, so that a step's inputs are copied in while
@@ -362,14 +411,9 @@ def run_native(args, rank, world):
     cls = [[cl, dev_inputs()], [cl2, dev_inputs()]]
     trs = [tr, tr2]
     reds = [(s_chi2, grad), (s_chi2_2, grad_2)]
-    out_views = lambda t_: (t_.label[:n_clusters], t_.trk_off[:cap_t + 1], t_.trk_hits[:n_clusters],
-                            t_.par[:cap_t * 5])
     stage = [[tuple(torch.empty_like(x) for x in out_views(tr)) + (torch.empty(74, dtype=torch.float64, device=dev),)
               for _ in range(2)] for _ in range(2)]
-    h_outs = [[(h_label, h_off, h_hits, h_par, h_red)] +
-              [tuple(torch.empty_like(x).pin_memory() for x in (h_label, h_off, h_hits, h_par, h_red))],
-              [tuple(torch.empty_like(x).pin_memory() for x in (h_label, h_off, h_hits, h_par, h_red))
-               for _ in range(2)]]
+    h_outs = [[h_seq, host_set()], [host_set(), host_set()]]
     ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
     ev_comp = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
     ev_out = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
@@ -387,14 +431,13 @@ def run_native(args, rank, world):
                 c.bin_off.copy_(h_bo, non_blocking=True)
                 ev_in[b][j].record(s_in)
             cs.wait_event(ev_in[b][j])
-            cx.tpc_track_batch(c, t_, stream=cs)
-            cx.tpc_refit_grad(c, t_, theta, sc, gr, w_batch, stream=cs)
+            cx.tpc_track_refit_batch(c, t_, theta, sc, gr, w_batch, stream=cs)
             cs.wait_event(ev_out[b][j])                   # this staging set is on the host already
             with torch.cuda.stream(cs):                   # results to device staging
-                for dst, src in zip(st[:4], out_views(t_)):
+                for dst, src in zip(st[:-1], out_views(t_)):
                     dst.copy_(src, non_blocking=True)
-                st[4][:1].copy_(sc, non_blocking=True)
-                st[4][1:].copy_(gr, non_blocking=True)
+                st[-1][:1].copy_(sc, non_blocking=True)
+                st[-1][1:].copy_(gr, non_blocking=True)
             ev_comp[b][j].record(cs)
             with torch.cuda.stream(s_out):                # staging to the host
                 s_out.wait_event(ev_comp[b][j])
@@ -425,8 +468,28 @@ def run_native(args, rank, world):
     ms_e2e = e0.elapsed_time(e1) / n_pipe
     assert ctx.tpc_sync_status() == 0 and ctx2.tpc_sync_status() == 0
     ms_e2e, _ = aggregate(ms_e2e, n_clusters, world, dev)
+    # every host result set (both contexts, both buffer sets: the last steps of the timed loop) must
+    # equal the device-resident result bit for bit; a race between a staging copy and the next
+    # step's outputs would show here
+    torch.cuda.synchronize()
+    nt, nh = res["n_tracks"], int(res["trk_off"][-1])
+    want = (res["label"][:n_clusters], res["trk_off"], res["trk_hits"], res["ev_trk_off"][:n_ev + 1],
+            res["par"].reshape(-1), res["xref"], res["cov"].reshape(-1), res["chi2"], res["ndf"],
+            np.array([nt], np.int32))
+    prefix = (n_clusters, nt + 1, nh, n_ev + 1, 5 * nt, nt, 15 * nt, nt, nt, 1)
+    e2e_checked = 0
+    for b in range(2):
+        for j in range(2):
+            ho = h_outs[b][j]
+            for k, (got, w_, m) in enumerate(zip(ho[:-1], want, prefix)):
+                if not np.array_equal(got[:m].numpy(), np.asarray(w_)[:m]):
+                    raise RuntimeError("end-to-end result %d of context %d, set %d differs from the device result"
+                                       % (k, b, j))
+            if not torch.equal(ho[-1], ref_red):
+                raise RuntimeError("end-to-end sum of chi2 / gradient of context %d, set %d differs" % (b, j))
+            e2e_checked += 1
 
-    out.update(ms_e2e=ms_e2e, ms_e2e_seq=ms_e2e_seq, h2d=h2d, d2h=d2h)
+    out.update(ms_e2e=ms_e2e, ms_e2e_seq=ms_e2e_seq, h2d=h2d, d2h=d2h, e2e_checked=e2e_checked)
     if rank != 0:
         return out
 
@@ -495,11 +558,34 @@ def run_native(args, rank, world):
     ctx.tpc_track_event(c5, t5)
     torch.cuda.synchronize()
     w5 = select(t5, int(t5.n_tracks.item()))
+    # references at the vertex from the TPC-ITS matching (inner-tracker tracks with 95 % efficiency
+    # and 2 % fakes, generated from the event's particles)
+    its5, its_part = synth.its_tracks(ev5)
+    its5_d = torch.tensor(its5.astype(np.float32), device=dev)
+    nt5 = int(t5.n_tracks.item())
+    m_trk = torch.empty(nt5, dtype=torch.int32, device=dev)
+    m_its = torch.empty(its5.shape[0], dtype=torch.int32, device=dev)
+    a5 = torch.zeros((nt5, 8), dtype=torch.float32, device=dev)
+    ms_match, _ = timed(lambda: ctx.tpc_its_match(c5, t5, its5_d, m_trk, m_its, a5), 10, 3)
+    ref5 = a5.cpu().numpy().astype(np.float64)
     h5 = t5.to_host()
-    ref5 = synth.vertex_references(ev5, h5["trk_off"], h5["trk_hits"])
-    a5 = torch.tensor(ref5.astype(np.float32), device=dev)
+    mt5 = m_trk.cpu().numpy()
+    lead5 = np.array([np.bincount(np.maximum(ev5.mc_track[h5["trk_hits"][a:b]], 0)).argmax()
+                      for a, b in zip(h5["trk_off"][:-1], h5["trk_off"][1:])])
+    mm = mt5 >= 0
+    match_out = {"ms_per_event": ms_match, "tracks": nt5, "its_tracks": int(its5.shape[0]),
+                 "matched": int(mm.sum()), "right_particle": float((its_part[mt5[mm]] == lead5[mm]).mean()),
+                 "to_fakes": int((its_part[mt5[mm]] < 0).sum()), "with_references": int((ref5[:, 0] > 0).sum())}
     th5 = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
+    # the adjoint as specified: per-row Kalman states recomputed in the reverse sweep from checkpoints
+    # (every 16 steps); then the variant that stores every step's input state (100 B per hit)
+    from paper_1712_09434_gb300 import tune as _tune
     ms_grad, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5, a5, 1), 10, 3)
+    g_ck = grad.clone()
+    ctx.tpc_set_tuning(_tune.to_struct({"refit_grad": (0, 0, 1)}))
+    ms_grad_stored, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5, a5, 1), 10, 3)
+    ctx.tpc_set_tuning(None)
+    assert torch.equal(g_ck, grad), "the two adjoint forms must give identical gradients"
 
     # plain per-event tracking of single events: the central event above and a 5,000-track event
     single = {}
@@ -510,6 +596,23 @@ def run_native(args, rank, world):
                               ("central_20000_tracks", c5, t5, ev5.n_clusters)]:
         ms_ev, _ = timed(lambda: ctx.tpc_track_event(cc, tt), 10, 3)
         single[name] = {"clusters": int(ncl), "ms": ms_ev, "clusters_per_s": ncl / (ms_ev * 1e-3)}
+
+    # rules for inefficient data (links across an empty row, gap merge inside a sector) on the
+    # central-shaped event with dead rows 60-61, 100-111 and 5 % of the crossings dropped
+    evi = synth.make_event(synth.inefficient_central())
+    ci = capi.Clusters.from_numpy(evi.pad_fp, evi.time_fp, evi.bin_off, 1)
+    ti = capi.Tracks(evi.n_clusters, 1, evi.n_clusters // 10 + 1024, evi.n_clusters)
+    rules_out = {"event": "central-shaped, 20000 tracks, dead rows 60-61 and 100-111, 5 % of crossings dropped",
+                 "clusters": int(evi.n_clusters)}
+    for name, rules in (("plain", 0), ("rules", capi.TPC_RULE_SKIP_ROW | capi.TPC_RULE_GAP_MERGE)):
+        ctx.tpc_set_rules(rules)
+        ms_r, _ = timed(lambda: ctx.tpc_track_event(ci, ti), 5, 2)
+        hi = ti.to_host()
+        eff, n_part, fake = synth.track_quality(evi, hi["trk_off"], hi["trk_hits"])
+        rules_out[name] = {"ms": ms_r, "tracks": hi["n_tracks"], "found_whole_efficiency": eff, "particles": n_part,
+                           "fake_fraction": fake}
+    ctx.tpc_set_rules(0)
+    del ci, ti
 
     # calibration recovery: 20 preconditioned gradient steps from the nominal theta
     from paper_1712_09434_gb300 import calib
@@ -522,13 +625,16 @@ def run_native(args, rank, world):
            for b in blocks]
     pull = np.abs(cres.theta - th_star) / cres.sigma
     calib_out = {"steps": 20, "gradient_calls": n_calls, "references_dropped": n_drop, "wall_s": t_cal,
-                 "objective": "-2 log L: raw errors through the transformation + vertex references",
+                 "objective": "-2 log L: raw errors through the transformation + references at the vertex "
+                              "from the TPC-ITS matching",
                  "remaining_distortion_per_block": dict(zip(["s_vd", "d_k", "a_k"], rem)),
                  "max_pull_per_block": dict(zip(["s_vd", "d_k", "a_k"], [float(pull[b].max()) for b in blocks])),
                  "sum_chi2_start_end": [cres.history[0][1], cres.history[-1][1]],
                  "tracks_with_reference": int((ref5[:, 0] > 0).sum())}
 
-    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
+    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, ms_grad_event_stored=ms_grad_stored, its_match=match_out,
+               inefficient=rules_out,
+               n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
                weighted_hits=weighted_hits,
                calib=calib_out, single=single, frame=frame_out,
                n_chains=n_chains, cand_hits=cand_hits)
@@ -545,8 +651,12 @@ FLOP_FWD, FLOP_ADJ, FLOP_SQRT_FWD = 461, 850, 434
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def stage_flops(u):
-    return {"refit": FLOP_SQRT_FWD * u["n_hits"], "refit_grad": (FLOP_FWD + FLOP_ADJ) * u["weighted_hits"]}
+def stage_flops(u, adjoint_form="checkpoints"):
+    """FP32 operations of the Kalman stages: the tracking refit runs the square-root forward step per
+    hit; the gradient runs the forward step, its adjoint and (checkpoint form) the forward step again
+    to recompute the states of each segment."""
+    per_hit = FLOP_FWD + FLOP_ADJ + (FLOP_FWD if adjoint_form == "checkpoints" else 0)
+    return {"refit": FLOP_SQRT_FWD * u["n_hits"], "refit_grad": per_hit * u["weighted_hits"]}
 
 
 # algorithmic bytes per stage (compulsory DRAM traffic of each stage's inputs and outputs)
@@ -576,13 +686,17 @@ def finish_native(args, res, world):
     stage_ms = {s: v / k for s, v in prof.items()}
     dom = max(stage_ms, key=lambda s: stage_ms[s])
     byts = stage_bytes(res)
-    flops = stage_flops(res)
+    n_launch, adj_form = launches_per_step(res["tuning"].get("best"))
+    flops = stage_flops(res, adj_form)
+    fp = res.get("fp32_peak")
+    if fp:
+        fp32_roof, fp32_kind = fp["tflops"], "measured (tpc_fma_peak, %s)" % fp["config"]
+    else:
+        fp32_roof, fp32_kind = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
     if dom in flops:       # FP32 arithmetic of the Kalman kernels: the FP32 pipe is the roof
         achieved = flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "algorithmic_flops": flops[dom]}
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_roof, "unit": "TFLOP/s",
+                "frac": achieved / fp32_roof, "peak_kind": fp32_kind, "algorithmic_flops": flops[dom]}
     else:
         achieved = byts[dom] / (stage_ms[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -605,8 +719,8 @@ def finish_native(args, res, world):
                    "l2": "not flushed between steps: each step reads its own device copy of the batch (134 MB of "
                          "clusters, above the 129 MB L2) and ~11 GB of workspace; single_stream flushes L2 "
                          "(256 MB write) before every step",
-                   "step": "tpc_track_batch (CUDA graph) + tpc_refit_grad over the batch; two batches in flight "
-                           "(two contexts, two streams, steps alternating)"},
+                   "step": "tpc_track_refit_batch: tracking + refit / adjoint of the batch as one CUDA graph "
+                           "launch; two batches in flight (two contexts, two streams, steps alternating)"},
         "single_stream": {"value": res["n_clusters_all"] / (res["ms_single"] * 1e-3), "unit": "clusters/s",
                           "ms_per_step": res["ms_single"],
                           "form": "one batch at a time on one stream, L2 flushed before every step"},
@@ -614,9 +728,17 @@ def finish_native(args, res, world):
                   "form": "tpc_track_event + tpc_refit_grad per event, same 64 events"},
         "batched_gain": res["n_clusters"] / (res["ms_single"] * 1e-3) / plain_value,
         "adjoint": {"value": res["ms_grad_event"] * 1e3, "unit": "us/event",
-                    "event": "central, 20000 tracks, injected calibration, references at the vertex",
-                    "tracks": res["n_tracks_c5"]},
+                    "event": "central, 20000 tracks, injected calibration, references at the vertex from the "
+                             "TPC-ITS matching",
+                    "tracks": res["n_tracks_c5"],
+                    "form": "refit + adjoint, Kalman states of the reverse sweep recomputed from checkpoints "
+                            "every 16 steps",
+                    "stored_states": {"value": res["ms_grad_event_stored"] * 1e3, "unit": "us/event",
+                                      "form": "variant storing every step's input state (100 B per hit); "
+                                              "identical gradient"}},
         "calibration": res["calib"],
+        "its_match": res.get("its_match"),
+        "inefficient_data": res.get("inefficient"),
         "single_event": res["single"],
         "time_frame": res["frame"],
         "stage_ms": stage_ms,
@@ -626,13 +748,21 @@ def finish_native(args, res, world):
                   "tracks": res["n_tracks"], "track_hits": res["n_hits"], "weighted_track_hits": res["weighted_hits"]},
         "roofline": dict(roof, traffic=traffic),
         "stage_tflops": {k: flops[k] / (stage_ms[k] * 1e-3) / 1e12 for k in flops if stage_ms.get(k, 0) > 0},
+        "stage_fp32_frac": {k: flops[k] / (stage_ms[k] * 1e-3) / 1e12 / fp32_roof for k in flops
+                            if stage_ms.get(k, 0) > 0},
+        "fp32_peak": fp if fp else {"tflops": FP32_PEAK_TFLOPS, "kind": fp32_kind},
+        "adjoint_form_in_step": adj_form,
         "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"],
                 "form": "through the binding from pinned host buffers; two contexts taking the steps in turn, "
                         "two input sets per context, results staged on the device; host copies on their "
-                        "own streams overlapping the compute",
+                        "own streams overlapping the compute; every step copies the whole result set back "
+                        "(labels, track offsets and hits, event offsets, parameters, reference x, "
+                        "covariances, chi2, ndf, track count, sum of chi2 and gradient)",
+                "checked": "%d host result sets equal to the device-resident result bit for bit" %
+                           res.get("e2e_checked", 0),
                 "sequential_value": n_cl_total / (res["ms_e2e_seq"] * 1e-3)},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": n_launch * args.steps,
         "clocks": res["clocks"],
     }
     return line
@@ -754,7 +884,16 @@ def main():
     ap.add_argument("--store-tuning", default=None, help="write the autotuned shapes to this JSON cache")
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain/adjoint/e2e/CPU legs); for profiling")
+    ap.add_argument("--fp32-peak", action="store_true",
+                    help="measure the FP32 FMA throughput of the GPU only (the roof of the Kalman stages)")
     args = ap.parse_args()
+    if args.fp32_peak:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"fp32_peak": fp32_peak(seconds=2.0)}), flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

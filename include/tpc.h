@@ -58,11 +58,14 @@ typedef struct {
     double  lsb_cm;           /* fixed-point unit of pad_fp and time_fp [cm]               */
 } tpc_geometry;
 
-/* Clusters of one event (n_events = 1) or of a batch of events (concatenated, see above). */
+/* Clusters of one event (n_events = 1) or of a batch of events (concatenated, see above).
+ * bin_off must run from 0 to n_clusters without decreasing.  Every call checks this on the device
+ * before any kernel indexes with it; an offset set that fails is reported as TPC_ERR_BOUNDS by
+ * tpc_sync_status (the call then finds no tracks and writes nothing outside its buffers). */
 typedef struct {
     const int16_t  *pad_fp;   /* [n_clusters]                                              */
     const uint16_t *time_fp;  /* [n_clusters]                                              */
-    const int32_t  *bin_off;  /* [n_events*n_sectors*n_rows + 1], nondecreasing, from 0    */
+    const int32_t  *bin_off;  /* [n_events*n_sectors*n_rows + 1], 0 .. n_clusters, nondecr. */
     int32_t n_events;
     int32_t n_clusters;
 } tpc_clusters;
@@ -95,9 +98,10 @@ typedef struct {
  * finding (index 1) chunk = 1 selects the variant that stages rows r+-1 of every bin in shared
  * memory by bulk copies (one CTA per bin) instead of reading them through L1 (one warp per bin,
  * lanes taking the bin's clusters in Z-slab order), and chunk = 2 the warp-per-bin variant whose
- * lanes take the clusters in cluster (Y, Z) order; for the gradient kernel (index 7) chunk = 1
- * recomputes the Kalman states of the reverse sweep from checkpoints every 16 steps instead of
- * storing the input state of every step (100 B per hit of workspace; the default).
+ * lanes take the clusters in cluster (Y, Z) order; for the gradient kernel (index 7) the default
+ * recomputes the Kalman states of the reverse sweep from checkpoints every 16 steps, and chunk = 1
+ * selects the variant that stores the input state of every step instead (100 B per hit of
+ * workspace, no recomputation; the same gradient bit for bit).
  * Launch shapes never change results. */
 typedef struct {
     int32_t block[TPC_N_TUNE];
@@ -162,6 +166,39 @@ int tpc_refit_grad(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, 
                    const float *weight, const float *anchor, int32_t error_model, double *sum_chi2, double *grad,
                    void *stream);
 
+/* One whole step as a single CUDA graph launch: the tracking of tpc_track_batch (S1-S8) followed by
+ * tpc_refit_grad (S0, S8, S9) on the tracks just found, captured together once per argument set and
+ * replayed (a call with other arguments captures again).  Arguments as for the two calls; the
+ * refit reads the track count from out->n_tracks on the device.  Results are bit-identical to the
+ * two calls made one after the other.  Errors: as tpc_track_batch and tpc_refit_grad. */
+int tpc_track_refit_batch(tpc_ctx *ctx, const tpc_clusters *in, tpc_tracks *out, const double *theta,
+                          const float *weight, const float *anchor, int32_t error_model, double *sum_chi2,
+                          double *grad, const tpc_tuning *tune, void *stream);
+
+/* TPC-ITS matching for the drift calibration (sections 2.1 and 6 of the paper: the TPC drift is
+ * calibrated by matching TPC tracks to tracks of the inner tracker, ITS).
+ *  - in: the clusters the tracks were found on; trk: tracks with their fit (trk_off, trk_hits, par,
+ *    cov, xref, ndf, n_tracks as a tracking call writes them).
+ *  - its: device float [n_its][8] = (phi0, z0, tan lambda, q/pT, sigma_phi0, sigma_z0, sigma_tl,
+ *    sigma_qpt): global azimuth of the momentum, z and direction at the production vertex, and their
+ *    errors.  n_its <= the context's chain capacity (clusters / 5), else TPC_ERR_CAPACITY.
+ *  - Rule: every fitted track is carried by the exact helix step (FP64) from its first hit to
+ *    x = 0 in the frame of that hit's sector k; an ITS track is taken in that frame as y = 0,
+ *    sin phi = sin(phi0 - alpha_k).  Candidates lie within 0.1 rad in azimuth, 0.1 in tan lambda and
+ *    2 cm in z (z is what the calibration corrects); chi2 over (y, sin phi, tan lambda, q/pT) with the
+ *    track's covariance plus (0.01 cm)^2 in y and the ITS errors, chi2 <= 100 (loose: before the
+ *    calibration the track parameters carry the distortion, and a tight gate would pick references
+ *    by their own noise).  Mutual best pairs by (floor(chi2 * 2^20), index) are matched.
+ *  - Outputs (device): match_trk [n_tracks] (ITS index or -1), match_its [n_its] (track or -1), and
+ *    if anchor is not NULL (float [n_tracks][8], 16-byte aligned) the reference measurements of
+ *    tpc_refit_grad for every matched track that starts within the first 8 pad rows, has at least
+ *    30 hits and |sin phi| < 0.9 at the vertex: (0.01, z0, sigma_z0, tan lambda, sigma_tl, q/pT,
+ *    sigma_qpt, 0); zeros for the others.
+ * Errors: INVALID_ARG, NOT_RESERVED, CAPACITY, CUDA; BOUNDS (a hit outside the clusters) via
+ * tpc_sync_status. */
+int tpc_its_match(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, const float *its, int32_t n_its,
+                  int32_t *match_trk, int32_t *match_its, float *anchor, void *stream);
+
 /* Time-frame slice merge (arxiv 1712.09434 section 3, its outlook for continuous readout: a time
  * frame of many overlapping collisions is cut along the drift-time axis, the slices are tracked
  * one by one, and the track segments are merged afterwards).
@@ -195,6 +232,30 @@ int tpc_merge_slices(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *sli
  * tpc_refit_grad, and tpc_track_batch with tune == NULL); NULL restores the library defaults.
  * The values are copied.  Errors: INVALID_ARG (a value outside the bounds of tpc_tuning). */
 int tpc_set_tuning(tpc_ctx *ctx, const tpc_tuning *tune);
+
+/* Optional rules for data with missing clusters (dead pad rows, cluster inefficiency): readings of
+ * the paper's CA on neighbouring pad rows and of its segment merging (section 3).  Bits:
+ *  - TPC_RULE_SKIP_ROW: a cluster whose neighbouring row r+1 (r-1) has no cluster inside the link
+ *    window |dY|, |dZ| <= 384 looks at row r+2 (r-2) with the window doubled; with the partners a and
+ *    b rows away the straight-line residual is e = b Yu + a Yd - (a+b) Yc (likewise in Z), the cut
+ *    6 (ey^2 + ez^2) <= (a^2 + b^2 + (a+b)^2) * 13600, the pair of minimum (D, u, d) wins.  Chains
+ *    may then skip a row; the following's filter steps once per row across it.
+ *  - TPC_RULE_GAP_MERGE: two accepted segments of one sector whose ends are k = 9..GAP_MAX rows apart
+ *    (at least 8 empty rows, which the following does not bridge) are joined when the integer filter
+ *    of each, run over its kept hits and extrapolated row by row across the gap under the
+ *    following's stop rules, meets the other's end within the following's radius after k - 1
+ *    misses (77 + 38 (k - 1) LSB); D is the sum of both squared distances, mutual best pairs by
+ *    (D, index).  For the sector merge a segment with a gap successor is no outer end and one with
+ *    a gap predecessor no first segment.
+ * 0 (the default) gives the plain readings.  The rules apply to later tracking calls of the context.
+ * Errors: INVALID_ARG (unknown bits). */
+#define TPC_RULE_SKIP_ROW  1
+#define TPC_RULE_GAP_MERGE 2
+int tpc_set_rules(tpc_ctx *ctx, int32_t rules);
+
+/* The rule bits and GAP_MAX, for comparison with an independent implementation.  Returns the count
+ * written (at most cap). */
+int tpc_rule_constants(int64_t *out, int32_t cap);
 
 /* Wait for `stream` and return the device status word of the last calls (then clear it). */
 int tpc_sync_status(tpc_ctx *ctx, void *stream);
@@ -241,6 +302,11 @@ int tpc_profile_read(tpc_ctx *ctx, double *ms, int32_t cap, int32_t *n_calls);
  *  - All calls on a device share the array: calls that overlap on the GPU (different streams,
  *    or graph launches running concurrently) race and corrupt each other's results.  The array
  *    keeps the last call's contents; the call clears what must start at zero.
+ *  - The device address found by the first call is kept for the life of the process.  A process
+ *    that resets a device (cudaDeviceReset) gets a new copy of the array at another address and
+ *    must not call this entry point on that device again.
+ *  - bin_off is checked as for tpc_track_event: an offset set that does not run from 0 to
+ *    n_clusters without decreasing sets TPC_ERR_BOUNDS in *status and no link is made.
  * Errors: INVALID_ARG, CAPACITY, CUDA. */
 #define TPC_NOALLOC_MAX_CLUSTERS (1 << 20)
 #define TPC_NOALLOC_MAX_BINS 16384
@@ -253,6 +319,14 @@ int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *in, int32_t 
  * (diagnostics).
  * Errors: INVALID_ARG, CUDA. */
 int tpc_selftest_wait_timeout(int32_t *status, int32_t spin_limit, void *stream);
+
+/* FP32 fused multiply-add throughput (diagnostic; the paper has no counterpart): the roof of the
+ * Kalman refit and its adjoint, which are FP32 arithmetic per thread.  Launches sms * ctas_per_sm
+ * CTAs of `threads` threads (multiple of 32, <= 256) that each run 8 independent FMA chains for
+ * iters * 16 steps and store one float each to out (device, [sms * ctas_per_sm * threads]);
+ * *flops (host) receives the floating-point operations of the launch (an FMA counts two).  Time
+ * it with events on `stream`.  Errors: INVALID_ARG, CUDA. */
+int tpc_fma_peak(float *out, int64_t iters, int32_t ctas_per_sm, int32_t threads, int64_t *flops, void *stream);
 
 /* Reading constants of the integer track finding, for comparison with an independent
  * implementation: W_LINK, D_MAX, N_SEED, M_MISS, W_F0, W_F1, V_MAX, N_MIN, W_MERGE, MERGE_XMAX,

@@ -314,6 +314,33 @@ def grad_fd(pad, tim, bin_off, trk_off, trk_hits, theta, h=(1e-6, 1e-4, 1e-4), g
     return grad
 
 
+def its_match(fit_out, first_sector, its, g=None):
+    """TPC-ITS matching at the vertex (see or_its_match): fit_out = fit(...) of the TPC tracks,
+    first_sector = sector of every track's first hit, its = [n_its, 8] ITS tracks.  Returns
+    (match of every TPC track (ITS index or -1), match of every ITS track (TPC index or -1), chi2 of
+    each match)."""
+    nt = int(fit_out["par"].shape[0])
+    its = np.ascontiguousarray(its, np.float64).reshape(-1, 8)
+    ni = its.shape[0]
+    mt = np.empty(max(nt, 1), np.int32)
+    mi = np.empty(max(ni, 1), np.int32)
+    c2 = np.zeros(max(nt, 1))
+    rc = lib().or_its_match(_geom(g), ctypes.c_int32(nt), _p(np.ascontiguousarray(fit_out["par"], np.float64)),
+                            _p(np.ascontiguousarray(fit_out["cov"], np.float64)),
+                            _p(np.ascontiguousarray(fit_out["xref"], np.float64)),
+                            _p(np.ascontiguousarray(fit_out["ndf"], np.int32)),
+                            _p(np.ascontiguousarray(first_sector, np.int32)), ctypes.c_int32(ni), _p(its),
+                            _p(mt), _p(mi), _p(c2))
+    assert rc == 0, rc
+    return mt[:nt], mi[:ni], c2[:nt]
+
+
+def its_constants():
+    buf = np.zeros(8)
+    k = lib().or_its_constants(_p(buf), ctypes.c_int(8))
+    return dict(zip(["SIGMA_Y", "DPHI", "DTL", "DZ", "CHI2"], buf[:k].tolist()))
+
+
 def rule_constants():
     buf = np.zeros(8, np.int64)
     k = lib().or_rule_constants(_p(buf), ctypes.c_int(8))

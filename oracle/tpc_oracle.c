@@ -1190,3 +1190,113 @@ int or_merge_decide(const or_geom_in *gin, int32_t ks, const int64_t *s_end, int
     return merge_decide(&g, ks, s_end[0], s_end[1], s_end[2], s_end[3], s_end[4], s_end[5], kt, t_first[0],
                         t_first[1], t_first[2], D);
 }
+
+/* ============================================================================================
+ * TPC-ITS matching for the drift calibration (sections 2.1 and 6: the TPC drift is calibrated by
+ * matching TPC tracks to the tracks of the inner tracker).  Reading: every fitted TPC track (state
+ * and covariance at its first hit, in the frame of that hit's sector) is extrapolated by the exact
+ * helix step to x = 0, the production vertex; an ITS track (global azimuth phi0 of the momentum, z0,
+ * tan lambda, q/pT at the vertex, with their errors) is expressed in the same frame, y = 0, sin phi =
+ * sin(phi0 - alpha_k).  The drift calibration is unknown when matching, so z is not compared
+ * beyond a loose window; the match chi2 is over (y, sin phi, tan lambda, q/pT) with the sum of the
+ * TPC covariance and the ITS errors (sigma_y = OR_ITS_SIGMA_Y at the vertex).  Candidates: azimuth
+ * within OR_ITS_DPHI, tan lambda within OR_ITS_DTL, z within OR_ITS_DZ; chi2 <= OR_ITS_CHI2.  Each
+ * side keeps its best partner by (floor(chi2 * 2^20), index); mutual best pairs are matched.
+ * ========================================================================================== */
+#define OR_ITS_SIGMA_Y 0.01
+#define OR_ITS_DPHI    0.1
+#define OR_ITS_DTL     0.1
+#define OR_ITS_DZ      2.0
+#define OR_ITS_CHI2    100.0
+
+/* a - 2 pi n, n the nearest integer (IEEE remainder): the angle wrapped into [-pi, pi] */
+static double wrap_pi(double a) { return remainder(a, 2.0 * OR_PI); }
+
+/* chi2 = d^T A^-1 d for a symmetric positive definite 4x4 A (Cholesky); returns -1 if A is not */
+static double chi2_4(double A[4][4], const double *d) {
+    double L[4][4] = {{0}};
+    for (int i = 0; i < 4; i++) {
+        for (int j = 0; j <= i; j++) {
+            double v = A[i][j];
+            for (int k = 0; k < j; k++) v -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (v <= 0.0) return -1.0;
+                L[i][i] = sqrt(v);
+            } else {
+                L[i][j] = v / L[j][j];
+            }
+        }
+    }
+    double y[4];
+    for (int i = 0; i < 4; i++) {
+        double v = d[i];
+        for (int k = 0; k < i; k++) v -= L[i][k] * y[k];
+        y[i] = v / L[i][i];
+    }
+    return y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3];
+}
+
+int or_its_match(const or_geom_in *gin, int32_t n_trk, const double *par, const double *cov, const double *xref,
+                 const int32_t *ndf, const int32_t *sector, int32_t n_its, const double *its, int32_t *match_trk,
+                 int32_t *match_its, double *chi2_out) {
+    or_geom g;
+    if (make_geom(gin, &g)) return -1;
+    int64_t *bt = (int64_t *)malloc(sizeof(int64_t) * (n_trk + 1));
+    int64_t *bi = (int64_t *)malloc(sizeof(int64_t) * (n_its + 1));
+    double *bchi = (double *)malloc(sizeof(double) * (n_trk + 1));
+    for (int32_t t = 0; t < n_trk; t++) { bt[t] = -1; match_trk[t] = -1; bchi[t] = 0.0; }
+    for (int32_t i = 0; i < n_its; i++) { bi[i] = -1; match_its[i] = -1; }
+    const int64_t SHIFT = (int64_t)1 << 32;
+    for (int32_t t = 0; t < n_trk; t++) {
+        if (ndf[t] <= 0) continue;
+        or_kf s;
+        memset(&s, 0, sizeof(s));
+        s.x = xref[t];
+        s.ok = 1;
+        s.frame = sector[t];
+        int m = 0;
+        for (int i = 0; i < 5; i++) s.p[i] = par[t * 5 + i];
+        for (int i = 0; i < 5; i++) for (int j = 0; j <= i; j++) { s.P[i][j] = s.P[j][i] = cov[t * 15 + m]; m++; }
+        kf_propagate(&g, &s, 0.0);
+        if (!s.ok) continue;
+        const double alpha = ((sector[t] % (g.n_sectors / 2)) + 0.5) * 2.0 * g.half_angle;
+        const double phi_t = alpha + asin(s.p[2]);
+        const int ix[4] = {0, 2, 3, 4};
+        for (int32_t i = 0; i < n_its; i++) {
+            const double *r = its + 8 * (int64_t)i;
+            if (fabs(wrap_pi(r[0] - phi_t)) > OR_ITS_DPHI) continue;
+            if (fabs(r[2] - s.p[3]) > OR_ITS_DTL || fabs(r[1] - s.p[1]) > OR_ITS_DZ) continue;
+            const double dphi = wrap_pi(r[0] - alpha);
+            const double d[4] = {s.p[0], s.p[2] - sin(dphi), s.p[3] - r[2], s.p[4] - r[3]};
+            const double ev[4] = {OR_ITS_SIGMA_Y * OR_ITS_SIGMA_Y, pow(cos(dphi) * r[4], 2), r[6] * r[6], r[7] * r[7]};
+            double A[4][4];
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++) A[a][b] = s.P[ix[a]][ix[b]] + (a == b ? ev[a] : 0.0);
+            const double c2 = chi2_4(A, d);
+            if (c2 < 0.0 || c2 > OR_ITS_CHI2) continue;
+            const int64_t q = (int64_t)floor(c2 * 1048576.0);
+            const int64_t kt = q * SHIFT + i, ki = q * SHIFT + t;
+            if (bt[t] < 0 || kt < bt[t]) { bt[t] = kt; bchi[t] = c2; }
+            if (bi[i] < 0 || ki < bi[i]) bi[i] = ki;
+        }
+    }
+    for (int32_t t = 0; t < n_trk; t++) {
+        if (bt[t] < 0) continue;
+        const int32_t i = (int32_t)(bt[t] % SHIFT);
+        if (bi[i] >= 0 && (int32_t)(bi[i] % SHIFT) == t && bi[i] / SHIFT == bt[t] / SHIFT) {
+            match_trk[t] = i;
+            match_its[i] = t;
+            if (chi2_out) chi2_out[t] = bchi[t];
+        }
+    }
+    free(bt); free(bi); free(bchi);
+    return 0;
+}
+
+int or_its_constants(double *out, int cap) {
+    const double v[] = {OR_ITS_SIGMA_Y, OR_ITS_DPHI, OR_ITS_DTL, OR_ITS_DZ, OR_ITS_CHI2};
+    int n = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < n && i < cap; i++) out[i] = v[i];
+    return n;
+}
+

@@ -24,6 +24,8 @@ TPC_ERR_NOT_RESERVED = -6
 TPC_N_TUNE = 8
 TPC_ERRORS_FIXED = 0
 TPC_ERRORS_RAW = 1
+TPC_RULE_SKIP_ROW = 1
+TPC_RULE_GAP_MERGE = 2
 TPC_NOALLOC_MAX_CLUSTERS = 1 << 20
 TPC_NOALLOC_MAX_BINS = 16384
 STAGES = ["grid", "links", "chains", "follow", "select", "merge", "refit", "pack", "refit_grad", "reduce"]
@@ -73,6 +75,8 @@ def _load():
                                     ctypes.POINTER(tpc_tuning), vp]
     lib.tpc_refit_grad.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp, i32,
                                    vp, vp, vp]
+    lib.tpc_track_refit_batch.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp,
+                                          i32, vp, vp, ctypes.POINTER(tpc_tuning), vp]
     lib.tpc_merge_slices.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), i32,
                                      ctypes.POINTER(tpc_tracks), vp]
     lib.tpc_sync_status.argtypes = [vp, vp]
@@ -81,8 +85,13 @@ def _load():
     lib.tpc_strerror.restype = ctypes.c_char_p
     lib.tpc_debug_copy.argtypes = [vp, i32, vp, i64, vp]
     lib.tpc_constants.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
+    lib.tpc_rule_constants.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
+    lib.tpc_its_match.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, i32, vp, vp, vp,
+                                  vp]
+    lib.tpc_set_rules.argtypes = [vp, i32]
     lib.tpc_links_noalloc.argtypes = [ctypes.POINTER(tpc_geometry), ctypes.POINTER(tpc_clusters), vp, vp, vp, vp]
     lib.tpc_selftest_wait_timeout.argtypes = [vp, i32, vp]
+    lib.tpc_fma_peak.argtypes = [vp, i64, i32, i32, ctypes.POINTER(i64), vp]
     lib.tpc_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.tpc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(i32)]
     return lib
@@ -106,6 +115,12 @@ def constants():
     names = ["W_LINK", "D_MAX", "N_SEED", "M_MISS", "W_F0", "W_F1", "V_MAX", "N_MIN", "W_MERGE",
              "MERGE_XMAX", "MERGE_BACK"]
     return dict(zip(names, [buf[i] for i in range(n)]))
+
+
+def rule_constants():
+    buf = (ctypes.c_int64 * 8)()
+    n = _lib.tpc_rule_constants(buf, 8)
+    return dict(zip(["RULE_SKIP_ROW", "RULE_GAP_MERGE", "GAP_MAX"], [buf[i] for i in range(n)]))
 
 
 def _ptr(t):
@@ -182,6 +197,15 @@ def tpc_links_noalloc(geometry, clusters, up, down, status=None, stream=None):
                                   _stream(stream))
 
 
+def tpc_fma_peak(out, iters, ctas_per_sm, threads, stream=None):
+    """Launch the FP32 FMA throughput kernel (see include/tpc.h); returns its floating-point
+    operations.  out: device float32 tensor of at least sms * ctas_per_sm * threads elements."""
+    flops = ctypes.c_int64(0)
+    check(_lib.tpc_fma_peak(_ptr(out), int(iters), int(ctas_per_sm), int(threads), ctypes.byref(flops),
+                            _stream(stream)), "tpc_fma_peak")
+    return int(flops.value)
+
+
 def default_geometry():
     return tpc_geometry(36, 159, 85.0, 247.0, 10.0, 250.0, 1.0 / 128.0)
 
@@ -233,11 +257,32 @@ class Context:
                                   _ptr(anchor), int(error_model), _ptr(sum_chi2), _ptr(grad), _stream(stream)),
               "tpc_refit_grad")
 
+    def tpc_track_refit_batch(self, clusters, tracks, theta, sum_chi2, grad=None, weight=None, anchor=None,
+                              error_model=TPC_ERRORS_FIXED, tuning=None, stream=None):
+        """Tracking + refit / adjoint of the tracks as one graph launch (see include/tpc.h)."""
+        cs, ts = clusters.struct(), tracks.struct()
+        check(_lib.tpc_track_refit_batch(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(theta), _ptr(weight),
+                                         _ptr(anchor), int(error_model), _ptr(sum_chi2), _ptr(grad),
+                                         ctypes.byref(tuning) if tuning is not None else ctypes.POINTER(tpc_tuning)(),
+                                         _stream(stream)),
+              "tpc_track_refit_batch")
+
+    def tpc_its_match(self, clusters, tracks, its, match_trk, match_its, anchor=None, stream=None):
+        """Match the fitted tracks to ITS tracks (device float32 [n_its, 8]); see include/tpc.h."""
+        cs, ts = clusters.struct(), tracks.struct()
+        n_its = int(its.shape[0]) if its is not None else 0
+        check(_lib.tpc_its_match(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(its), n_its, _ptr(match_trk),
+                                 _ptr(match_its), _ptr(anchor), _stream(stream)), "tpc_its_match")
+
     def tpc_merge_slices(self, clusters, slice_tracks, slice_len, frame, stream=None):
         """Join the tracks of consecutive time slices into frame tracks (see tpc_merge_slices)."""
         cs, ss, fs = clusters.struct(), slice_tracks.struct(), frame.struct()
         check(_lib.tpc_merge_slices(self.handle, ctypes.byref(cs), ctypes.byref(ss), int(slice_len), ctypes.byref(fs),
                                     _stream(stream)), "tpc_merge_slices")
+
+    def tpc_set_rules(self, rules=0):
+        """TPC_RULE_SKIP_ROW | TPC_RULE_GAP_MERGE for data with missing clusters (0: plain readings)."""
+        check(_lib.tpc_set_rules(self.handle, int(rules)), "tpc_set_rules")
 
     def tpc_set_tuning(self, tuning=None):
         check(_lib.tpc_set_tuning(self.handle, ctypes.byref(tuning) if tuning is not None

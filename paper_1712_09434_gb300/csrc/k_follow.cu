@@ -18,9 +18,11 @@ struct Abg {
     long long p, v, a;
 };
 
-__device__ __forceinline__ void abg_init(Abg &f, long long m0, long long m1) {
+// state at m0 with the velocity of the step to m1, drow = 1 or 2 rows further (2 across a row that
+// a link skips; the division is exact)
+__device__ __forceinline__ void abg_init(Abg &f, long long m0, long long m1, int drow) {
     f.p = m0 * 65536;
-    f.v = (m1 - m0) * 65536;
+    f.v = (m1 - m0) * (65536 / drow);
     f.a = 0;
 }
 __device__ __forceinline__ void abg_predict(Abg &f) {
@@ -110,6 +112,7 @@ __global__ void __launch_bounds__(128) k_follow(Work W) {
     const DevGeom &g = *W.geom;
     const int nr = g.n_rows;
     const int lane = threadIdx.x & 31;
+    const bool skip = (W.rules & TPC_RULE_SKIP_ROW) != 0;
     int n_chains = W.counters[CNT_NCHAINS];
     if (n_chains > W.cap_chains) n_chains = W.cap_chains;
     const int chunk = 32 * (W.tune.chunk[3] > 0 ? W.tune.chunk[3] : 1);
@@ -124,45 +127,65 @@ __global__ void __launch_bounds__(128) k_follow(Work W) {
             const int row0 = bin % nr;
             const int rowbase = bin - row0;
             int32_t *slots = W.cand_slots + (size_t)t * nr;
-            // filter along the chain in ascending rows, writing the chain hits
+            // filter along the chain in ascending rows, writing the chain hits (one filter step per
+            // pad row: a row skipped by a link is a prediction without an update and a -1 slot)
             Abg fy, fz;
-            int x = start, m0y = 0, m0z = 0;
+            int x = start, m0y = 0, m0z = 0, row = row0, rprev = row0;
             for (int k = 0; k < len; k++) {
                 const int y = __ldg(W.pad + x), z = __ldg(W.tim + x);
-                slots[row0 + k] = x;
+                slots[row] = x;
+                const int d = row - rprev;
                 if (k == 0) {
                     m0y = y;
                     m0z = z;
-                } else if (k == 1) {
-                    // state at the first hit with velocity m1 - m0, then the regular step to m1
-                    abg_init(fy, m0y, y);
-                    abg_init(fz, m0z, z);
-                    abg_predict(fy);
-                    abg_predict(fz);
-                    abg_update(fy, y);
-                    abg_update(fz, z);
                 } else {
-                    abg_predict(fy);
-                    abg_predict(fz);
+                    if (k == 1) {   // state at the first hit with the velocity of the step to the second
+                        abg_init(fy, m0y, y, d);
+                        abg_init(fz, m0z, z, d);
+                    }
+                    for (int j = 0; j < d; j++) {
+                        abg_predict(fy);
+                        abg_predict(fz);
+                    }
                     abg_update(fy, y);
                     abg_update(fz, z);
                 }
-                if (k + 1 < len) x = W.up[x];
+                rprev = row;
+                if (k + 1 < len) {
+                    x = W.up[x];
+                    // the next hit is one row further, or two across a row the link skips
+                    if (skip && row + 2 < nr && x >= __ldg(W.bin_off + rowbase + row + 2)) {
+                        slots[row + 1] = -1;
+                        row += 2;
+                    } else {
+                        row += 1;
+                    }
+                }
             }
-            const int row_last = row0 + len - 1;
+            const int row_last = row;
             int r1, r0;
             const int n_out = extend(W, g, fy, fz, rowbase, row_last, +1, slots, &r1);
-            // filter along the chain in descending rows
+            // filter along the chain in descending rows from its last two hits
             {
-                const int h1 = slots[row_last], h2 = slots[row_last - 1];
-                abg_init(fy, __ldg(W.pad + h1), __ldg(W.pad + h2));
-                abg_init(fz, __ldg(W.tim + h1), __ldg(W.tim + h2));
-                for (int k = len - 2; k >= 0; k--) {
-                    const int h = slots[row0 + k];
-                    abg_predict(fy);
-                    abg_predict(fz);
+                const int h1 = slots[row_last];
+                int rp = row_last;
+                bool first = true;
+                for (int r = row_last - 1; r >= row0; r--) {
+                    const int h = slots[r];
+                    if (h < 0) continue;
+                    const int d = rp - r;
+                    if (first) {
+                        abg_init(fy, __ldg(W.pad + h1), __ldg(W.pad + h), d);
+                        abg_init(fz, __ldg(W.tim + h1), __ldg(W.tim + h), d);
+                        first = false;
+                    }
+                    for (int j = 0; j < d; j++) {
+                        abg_predict(fy);
+                        abg_predict(fz);
+                    }
                     abg_update(fy, __ldg(W.pad + h));
                     abg_update(fz, __ldg(W.tim + h));
+                    rp = r;
                 }
             }
             const int n_in = extend(W, g, fy, fz, rowbase, row0, -1, slots, &r0);

@@ -139,13 +139,27 @@ __device__ __forceinline__ int lower_y(const int32_t *yz, int lo, int hi, int y)
     return lo;
 }
 
+// Whether a row holds a cluster inside the window |dY|, |dZ| <= w around (yc, zc).
+__device__ __forceinline__ bool any_in_window(const RowView &rv, int yc, int zc, int w) {
+    const int zl = slab_of(max(zc - w, 0)), zh = slab_of(zc + w);
+    for (int s = zl; s <= zh; s++) {
+        const int hi = rv.zo[s + 1];
+        for (int i = lower_y(rv.yz, rv.zo[s], hi, yc - w); i < hi; i++) {
+            const int32_t v = rv.yz[i];
+            if ((int16_t)(v & 0xffff) > yc + w) break;
+            if (abs((int)((uint32_t)v >> 16) - zc) <= w) return true;
+        }
+    }
+    return false;
+}
+
 // Warp per row bin, taken from a queue (no CTA barriers: each warp runs at its own pace); the lanes
 // take the bin's clusters 32 at a time and read the neighbouring rows' grid data through L1.
 // SLAB_ORDER (the default): the lanes take the clusters in the order of the bin's own grid (Z slab,
 // then Y), so that the 32 clusters of a warp search the same slabs of rows r+-1 at neighbouring Y
 // (12 % faster on the 64-event batch, 23 % on dense time-frame slices); otherwise in cluster
 // (Y, Z) order.
-template <bool SLAB_ORDER>
+template <bool SLAB_ORDER, bool SKIP>
 __global__ void __launch_bounds__(LINK_BLOCK) k_links(Work W) {
     // down-row candidates of each lane's cluster: packed (Y, Z) and row-local index, [k][thread]
     __shared__ int32_t s_dv[LINK_DCAP][LINK_BLOCK];
@@ -165,10 +179,14 @@ __global__ void __launch_bounds__(LINK_BLOCK) k_links(Work W) {
             for (int c = c0 + lane; c < c1; c += 32) { W.up[c] = -1; W.down[c] = -1; }
             continue;
         }
-        RowView rv[2];
-        int cb[2];
-        for (int k = 0; k < 2; k++) {
-            const int bb = k == 0 ? b - 1 : b + 1;          // 0: down row, 1: up row
+        // rows r-1, r+1 and, with the skip-row rule, r-2 and r+2 (where they exist)
+        constexpr int NR = SKIP ? 4 : 2;
+        RowView rv[NR];
+        int cb[NR];
+        const bool has2[2] = {SKIP && r >= 2, SKIP && r + 2 <= g.n_rows - 1};
+        for (int k = 0; k < NR; k++) {
+            const int bb = k == 0 ? b - 1 : k == 1 ? b + 1 : k == 2 ? b - 2 : b + 2;
+            if (k >= 2 && !has2[k - 2]) { cb[k] = 0; continue; }
             cb[k] = __ldg(W.bin_off + bb);
             const int ps = pstart_of(cb[k], bb);
             rv[k].yz = W.gyz + ps;
@@ -189,25 +207,36 @@ __global__ void __launch_bounds__(LINK_BLOCK) k_links(Work W) {
                 yc = W.pad[c];
                 zc = W.tim[c];
             }
-            const int zl = slab_of(max(zc - W_LINK, 0)), zh = slab_of(zc + W_LINK);
+            // each side: the neighbouring row, or (skip-row rule) the row after it with the window
+            // doubled when the neighbouring row has no cluster inside the window; fb, fa are the row
+            // distances of the down and up partners
+            int kd = 0, ku = 1, wd = W_LINK, wu = W_LINK, fb = 1, fa = 1;
+            if constexpr (SKIP) {
+                if (has2[0] && !any_in_window(rv[0], yc, zc, W_LINK)) { kd = 2; wd = 2 * W_LINK; fb = 2; }
+                if (has2[1] && !any_in_window(rv[1], yc, zc, W_LINK)) { ku = 3; wu = 2 * W_LINK; fa = 2; }
+            }
+            const RowView dv = rv[kd], uv = rv[ku];
+            const int kcut = fa * fa + fb * fb + (fa + fb) * (fa + fb);   // 6 for neighbouring rows
+            const int zld = slab_of(max(zc - wd, 0)), zhd = slab_of(zc + wd);
+            const int zlu = slab_of(max(zc - wu, 0)), zhu = slab_of(zc + wu);
             // down-row candidates inside the window, LINK_DCAP at a time in shared memory; every chunk
             // is compared with all up-row candidates (a window rarely holds more than one chunk).
-            // |ey|, |ez| <= 2 W_LINK, so D fits 32 bits.
+            // |ey|, |ez| <= 3072, so D fits 32 bits.
             unsigned long long best = ~0ull;
             int nd_all = 0;
             for (int base = 0; base == 0 || base < nd_all; base += LINK_DCAP) {
                 int k = 0;
-                for (int sd = zl; sd <= zh; sd++) {
-                    const int hd = rv[0].zo[sd + 1];
-                    for (int id = lower_y(rv[0].yz, rv[0].zo[sd], hd, yc - W_LINK); id < hd; id++) {
-                        const int32_t vd = rv[0].yz[id];
+                for (int sd = zld; sd <= zhd; sd++) {
+                    const int hd = dv.zo[sd + 1];
+                    for (int id = lower_y(dv.yz, dv.zo[sd], hd, yc - wd); id < hd; id++) {
+                        const int32_t vd = dv.yz[id];
                         const int yd = (int16_t)(vd & 0xffff);
-                        if (yd > yc + W_LINK) break;
+                        if (yd > yc + wd) break;
                         const int zd = (int)((uint32_t)vd >> 16);
-                        if (abs(zd - zc) > W_LINK) continue;
+                        if (abs(zd - zc) > wd) continue;
                         if (k >= base && k < base + LINK_DCAP) {
                             s_dv[k - base][threadIdx.x] = vd;
-                            s_dl[k - base][threadIdx.x] = rv[0].loc[id];
+                            s_dl[k - base][threadIdx.x] = dv.loc[id];
                         }
                         k++;
                     }
@@ -215,21 +244,21 @@ __global__ void __launch_bounds__(LINK_BLOCK) k_links(Work W) {
                 nd_all = k;
                 const int nd = min(nd_all - base, LINK_DCAP);
                 if (nd <= 0) break;
-                for (int su = zl; su <= zh; su++) {
-                    const int hi = rv[1].zo[su + 1];
-                    for (int iu = lower_y(rv[1].yz, rv[1].zo[su], hi, yc - W_LINK); iu < hi; iu++) {
-                        const int32_t vu = rv[1].yz[iu];
+                for (int su = zlu; su <= zhu; su++) {
+                    const int hi = uv.zo[su + 1];
+                    for (int iu = lower_y(uv.yz, uv.zo[su], hi, yc - wu); iu < hi; iu++) {
+                        const int32_t vu = uv.yz[iu];
                         const int yu = (int16_t)(vu & 0xffff);
-                        if (yu > yc + W_LINK) break;
+                        if (yu > yc + wu) break;
                         const int zu = (int)((uint32_t)vu >> 16);
-                        if (abs(zu - zc) > W_LINK) continue;
-                        const unsigned long long lu = (unsigned long long)rv[1].loc[iu] << 16;
+                        if (abs(zu - zc) > wu) continue;
+                        const unsigned long long lu = (unsigned long long)uv.loc[iu] << 16;
                         for (int kk = 0; kk < nd; kk++) {
                             const int32_t vd = s_dv[kk][threadIdx.x];
-                            const int ey = yu + (int16_t)(vd & 0xffff) - 2 * yc;
-                            const int ez = zu + (int)((uint32_t)vd >> 16) - 2 * zc;
+                            const int ey = fb * yu + fa * (int16_t)(vd & 0xffff) - (fa + fb) * yc;
+                            const int ez = fb * zu + fa * (int)((uint32_t)vd >> 16) - (fa + fb) * zc;
                             const int D = ey * ey + ez * ez;
-                            if (D > D_MAX) continue;
+                            if (6 * D > kcut * D_MAX) continue;
                             const unsigned long long key = ((unsigned long long)D << 32) | lu | s_dl[kk][threadIdx.x];
                             best = key < best ? key : best;
                         }
@@ -237,8 +266,8 @@ __global__ void __launch_bounds__(LINK_BLOCK) k_links(Work W) {
                 }
             }
             if (best != ~0ull) {
-                W.up[c] = cb[1] + (int)((best >> 16) & 0xffff);
-                W.down[c] = cb[0] + (int)(best & 0xffff);
+                W.up[c] = cb[ku] + (int)((best >> 16) & 0xffff);
+                W.down[c] = cb[kd] + (int)(best & 0xffff);
             } else {
                 W.up[c] = -1;
                 W.down[c] = -1;
@@ -394,6 +423,37 @@ __global__ void __launch_bounds__(128) k_links_staged(Work W) {
 
 }  // namespace
 
+// Bin offsets from the caller are checked before any stage indexes with them: 0 = bin_off[0] <=
+// bin_off[1] <= ... <= bin_off[nbins] = n_clusters.  A failing set raises ST_BOUNDS and is
+// replaced by one that puts every cluster in the last bin (the outermost row of the last sector,
+// which takes no links), so that every later stage stays inside its buffers and finds no tracks.
+__global__ void k_bins_check(const int32_t *in, int nbins, int n, int32_t *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nbins; i += gridDim.x * blockDim.x) {
+        const int v = in[i];
+        bool ok = v >= 0 && v <= n;
+        if (i == 0) ok = ok && v == 0;
+        if (i == nbins) ok = ok && v == n;
+        else ok = ok && v <= in[i + 1];
+        if (!ok) atomicOr(bad, 1);
+    }
+}
+
+__global__ void k_bins_copy(const int32_t *in, int32_t *out, int nbins, int n, const int32_t *bad, int32_t *status) {
+    const bool b = *bad != 0;
+    if (b && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_BOUNDS);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nbins; i += gridDim.x * blockDim.x)
+        out[i] = b ? (i == nbins ? n : 0) : in[i];
+}
+
+void launch_bins_check(const Work &W, cudaStream_t s) {
+    int grid = (W.nbins + 1 + 255) / 256;
+    if (grid > W.sm_count * 4) grid = W.sm_count * 4;
+    if (grid < 1) grid = 1;
+    k_bins_check<<<grid, 256, 0, s>>>(W.bin_off_in, W.nbins, W.n_clusters, W.counters + CNT_BINS_BAD);
+    k_bins_copy<<<grid, 256, 0, s>>>(W.bin_off_in, W.bin_ok, W.nbins, W.n_clusters, W.counters + CNT_BINS_BAD,
+                                     W.status);
+}
+
 void launch_grid(const Work &W, cudaStream_t s) {
     const int block = W.tune.block[0] > 0 ? W.tune.block[0] : 256;
     const int warps = block / 32;
@@ -408,7 +468,8 @@ void prepare_kernels() {
 }
 
 void launch_links(const Work &W, cudaStream_t s) {
-    if (W.tune.chunk[1] == 1) {     // rows staged in shared memory, CTA per bin
+    // the staged variant implements the plain reading only: the skip-row rule takes the L1 kernel
+    if (W.tune.chunk[1] == 1 && !(W.rules & TPC_RULE_SKIP_ROW)) {     // rows staged in shared memory, CTA per bin
         const int block = W.tune.block[1] > 0 ? W.tune.block[1] : 128;
         int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 8;
         if (grid > W.nbins) grid = W.nbins > 0 ? W.nbins : 1;
@@ -419,10 +480,11 @@ void launch_links(const Work &W, cudaStream_t s) {
     int grid = W.tune.grid[1] > 0 ? W.tune.grid[1] : W.sm_count * 16;
     const int warps = block / 32;
     if (grid * warps > W.nbins) grid = W.nbins > 0 ? (W.nbins + warps - 1) / warps : 1;
+    const bool skip = (W.rules & TPC_RULE_SKIP_ROW) != 0;
     if (W.tune.chunk[1] == 2)       // lanes in cluster (Y, Z) order
-        k_links<false><<<grid, block, 0, s>>>(W);
+        skip ? k_links<false, true><<<grid, block, 0, s>>>(W) : k_links<false, false><<<grid, block, 0, s>>>(W);
     else
-        k_links<true><<<grid, block, 0, s>>>(W);
+        skip ? k_links<true, true><<<grid, block, 0, s>>>(W) : k_links<true, false><<<grid, block, 0, s>>>(W);
 }
 
 }  // namespace tpc
@@ -443,7 +505,9 @@ namespace {
 constexpr int NOALLOC_NPAD = TPC_NOALLOC_MAX_CLUSTERS + 8 * (TPC_NOALLOC_MAX_BINS + 2) + 64;
 constexpr size_t NOALLOC_OFF_GEOM = 0;                                          // DevGeom
 constexpr size_t NOALLOC_OFF_CNT = (sizeof(DevGeom) + 255) & ~(size_t)255;      // counters[64]
-constexpr size_t NOALLOC_OFF_ZOFF = NOALLOC_OFF_CNT + 256;
+constexpr size_t NOALLOC_OFF_BINS = NOALLOC_OFF_CNT + 256;                       // checked bin_off
+constexpr size_t NOALLOC_OFF_ZOFF =
+    (NOALLOC_OFF_BINS + ((size_t)TPC_NOALLOC_MAX_BINS + 1) * 4 + 255) & ~(size_t)255;
 constexpr size_t NOALLOC_OFF_GYZ =
     (NOALLOC_OFF_ZOFF + (size_t)TPC_NOALLOC_MAX_BINS * ZOFF_STRIDE * 2 + 255) & ~(size_t)255;
 constexpr size_t NOALLOC_OFF_GLOC = (NOALLOC_OFF_GYZ + (size_t)NOALLOC_NPAD * 4 + 255) & ~(size_t)255;
@@ -525,7 +589,9 @@ extern "C" int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *i
     std::memset(&W, 0, sizeof(W));
     W.pad = in->pad_fp;
     W.tim = in->time_fp;
-    W.bin_off = in->bin_off;
+    W.bin_off_in = in->bin_off;
+    W.bin_ok = reinterpret_cast<int32_t *>(base + NOALLOC_OFF_BINS);
+    W.bin_off = W.bin_ok;
     W.n_events = in->n_events;
     W.n_clusters = in->n_clusters;
     W.nbins = (int)nbins;
@@ -541,6 +607,7 @@ extern "C" int tpc_links_noalloc(const tpc_geometry *geom, const tpc_clusters *i
     W.down = down;
     W.sm_count = sms;
     k_noalloc_setup<<<1, 64, 0, s>>>(base, geom->n_sectors, geom->n_rows);
+    launch_bins_check(W, s);
     launch_grid(W, s);
     launch_links(W, s);
     if (status) {

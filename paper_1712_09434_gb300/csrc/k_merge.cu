@@ -82,6 +82,155 @@ __global__ void k_merge_fill(Work W) {
     }
 }
 
+// ---- gap merge inside a sector (TPC_RULE_GAP_MERGE) --------------------------------------------
+// The integer steady-state filter of the following (alpha-beta-gamma 1/2, 1/8, 1/32, Q16, floor
+// shifts) runs over the kept hits of a segment, one step per pad row and an update per kept hit.
+struct Abg {
+    long long p, v, a;
+};
+__device__ __forceinline__ void abg_init(Abg &f, long long m0, long long m1, long long drow) {
+    f.p = m0 * 65536;
+    f.v = floor_div((m1 - m0) * 65536, drow);
+    f.a = 0;
+}
+__device__ __forceinline__ void abg_predict(Abg &f) {
+    f.p += f.v + (f.a >> 1);
+    f.v += f.a;
+}
+__device__ __forceinline__ void abg_update(Abg &f, long long m) {
+    const long long e = m * 65536 - f.p;
+    f.p += e >> 1;
+    f.v += e >> 3;
+    f.a += e >> 5;
+}
+__device__ __forceinline__ long long q16_round(long long p) { return (p + 32768) >> 16; }
+__device__ __forceinline__ bool gap_inside(const DevGeom &g, const Abg &fy, const Abg &fz, int row) {
+    const long long py = q16_round(fy.p), pz = q16_round(fz.p);
+    const long long av = fy.v < 0 ? -fy.v : fy.v;
+    return !((py < 0 ? -py : py) > g.ymax[row] || pz < 0 || pz > g.zmax || av > (long long)V_MAX * 65536);
+}
+
+// Backward filter of every accepted segment over its kept hits in descending rows: the state at its
+// first kept hit.  Also resets the gap keys.
+__global__ void k_gap_back(Work W) {
+    const int n = n_chains_of(W);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        W.gap_bestT[t] = ~0ull;
+        W.gap_bestS[t] = ~0ull;
+        if (W.seg_n[t] < N_MIN) continue;
+        const uint32_t key = key_of(W.nr, W.cand_n[t], t - sector_base(W, t));
+        const int rr = W.cand_rows[t];
+        const int32_t *sl = W.cand_slots + (size_t)t * W.nr;
+        Abg fy{}, fz{};
+        int k = 0, rprev = 0, h0 = -1;
+        for (int r = rr >> 16; r >= (rr & 0xffff); r--) {
+            const int h = sl[r];
+            if (h < 0 || W.owner[h] != key) continue;
+            if (k == 0) {
+                h0 = h;
+            } else if (k == 1) {
+                abg_init(fy, W.pad[h0], W.pad[h], rprev - r);
+                abg_init(fz, W.tim[h0], W.tim[h], rprev - r);
+                for (int j = rprev - r; j > 0; j--) { abg_predict(fy); abg_predict(fz); }
+                abg_update(fy, W.pad[h]);
+                abg_update(fz, W.tim[h]);
+            } else {
+                for (int j = rprev - r; j > 0; j--) { abg_predict(fy); abg_predict(fz); }
+                abg_update(fy, W.pad[h]);
+                abg_update(fz, W.tim[h]);
+            }
+            rprev = r;
+            k++;
+        }
+        long long *st = W.gap_state + 6 * (size_t)t;
+        st[0] = fy.p; st[1] = fy.v; st[2] = fy.a;
+        st[3] = fz.p; st[4] = fz.v; st[5] = fz.a;
+    }
+}
+
+// Thread per segment S: forward filter over its kept hits, then row by row across the gap; every
+// segment T of the same sector whose first kept hit lies k >= M_MISS + 1 rows past S's last kept
+// hit is tested both ways; (D, T) kept for S, (D, S) offered to T by 64-bit atomicMin.
+__global__ void k_gap_match(Work W) {
+    const DevGeom &g = *W.geom;
+    const int n = n_chains_of(W);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (W.seg_n[s] < N_MIN) continue;
+        const uint32_t key = key_of(W.nr, W.cand_n[s], s - sector_base(W, s));
+        const int rr = W.cand_rows[s];
+        const int32_t *sl = W.cand_slots + (size_t)s * W.nr;
+        Abg fy{}, fz{};
+        int k = 0, rprev = 0, h0 = -1, hl = -1;
+        for (int r = rr & 0xffff; r <= (rr >> 16); r++) {
+            const int h = sl[r];
+            if (h < 0 || W.owner[h] != key) continue;
+            if (k == 0) {
+                h0 = h;
+            } else {
+                if (k == 1) {
+                    abg_init(fy, W.pad[h0], W.pad[h], r - rprev);
+                    abg_init(fz, W.tim[h0], W.tim[h], r - rprev);
+                }
+                for (int j = r - rprev; j > 0; j--) { abg_predict(fy); abg_predict(fz); }
+                abg_update(fy, W.pad[h]);
+                abg_update(fz, W.tim[h]);
+            }
+            rprev = r;
+            hl = h;
+            k++;
+        }
+        const int rs = rprev;
+        const long long ys = W.pad[hl], zs = W.tim[hl];
+        const int b0 = W.chain_bin[s] - W.chain_bin[s] % W.nr;   // (event, sector) row 0
+        unsigned long long best = ~0ull;
+        for (int rt = rs + 1; rt < W.nr && rt <= rs + GAP_MAX; rt++) {
+            abg_predict(fy);
+            abg_predict(fz);
+            if (!gap_inside(g, fy, fz, rt)) break;
+            if (rt - rs - 1 < M_MISS) continue;
+            const long long py = q16_round(fy.p), pz = q16_round(fz.p);
+            const long long w = W_F0 + (long long)W_F1 * (rt - rs - 1);
+            for (int i = W.mrg_off[b0 + rt]; i < W.mrg_off[b0 + rt + 1]; i++) {
+                const int t = W.mrg_list[i];
+                if (t == s) continue;
+                const int4 e = W.inend[t];
+                const long long dy = e.y - py, dz = e.z - pz;
+                if (dy > w || dy < -w || dz > w || dz < -w || dy * dy + dz * dz > w * w) continue;
+                const long long *st = W.gap_state + 6 * (size_t)t;
+                Abg by{st[0], st[1], st[2]}, bz{st[3], st[4], st[5]};
+                bool inside = true;
+                for (int j = 1; j <= rt - rs && inside; j++) {
+                    abg_predict(by);
+                    abg_predict(bz);
+                    inside = gap_inside(g, by, bz, rt - j);
+                }
+                if (!inside) continue;
+                const long long ey = ys - q16_round(by.p), ez = zs - q16_round(bz.p);
+                if (ey > w || ey < -w || ez > w || ez < -w || ey * ey + ez * ez > w * w) continue;
+                const unsigned long long D = (unsigned long long)(dy * dy + dz * dz + ey * ey + ez * ez);
+                const unsigned long long kT = (D << 32) | (unsigned)t;
+                best = kT < best ? kT : best;
+                atomicMin(W.gap_bestS + t, (D << 32) | (unsigned)s);
+            }
+        }
+        W.gap_bestT[s] = best;
+    }
+}
+
+// Mutual best gap pairs become merge links S -> T before the sector merge runs.
+__global__ void k_gap_link(Work W) {
+    const int n = n_chains_of(W);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const unsigned long long v = W.gap_bestT[s];
+        if (v == ~0ull) continue;
+        const int t = (int)(v & 0xffffffffu);
+        if (W.gap_bestS[t] == ((v & 0xffffffff00000000ull) | (unsigned)s)) {
+            W.next[s] = t;
+            W.prev[t] = s;
+        }
+    }
+}
+
 // One warp per outer end S: the lanes take the candidate segments T of the reachable rows of both
 // adjacent sectors 32 at a time; the warp keeps the minimum (D, T) for S and every valid pair offers
 // (D, S) to T with a 64-bit atomicMin.
@@ -93,7 +242,7 @@ __global__ void k_merge_match(Work W) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const float pitch = (float)(g.xtab[W.nr - 1] - g.xtab[0]) / (float)(W.nr - 1);
     for (int s = gw; s < n; s += nw) {
-        if (W.seg_n[s] < N_MIN) continue;
+        if (W.seg_n[s] < N_MIN || W.next[s] >= 0) continue;   // a gap successor: no outer end
         const int4 p1 = W.outend[2 * s], p2 = W.outend[2 * s + 1];
         const int ks = p1.w;
         const int ev = W.chain_bin[s] / (W.ns * W.nr);
@@ -132,6 +281,7 @@ __global__ void k_merge_match(Work W) {
             const int i1 = W.mrg_off[b0 + r_hi + 1];
             for (int i = W.mrg_off[b0 + r_lo] + lane; i < i1; i += 32) {
                 const int t = W.mrg_list[i];
+                if (W.prev[t] >= 0) continue;                        // a gap predecessor: no first segment
                 const int4 e = W.inend[t];
                 const long long XT = e.x;
                 const long long ax = XT - x2;
@@ -272,6 +422,11 @@ void launch_merge(const Work &W, cudaStream_t s) {
     scan_exclusive(W.bin_cnt, W.mrg_off, W.nbins, nullptr, nullptr, W.scan_tmp, W.scan_tmp_len, s);
     cudaMemsetAsync(W.bin_cnt, 0, sizeof(int32_t) * (W.nbins + 1), s);
     k_merge_fill<<<grid, block, 0, s>>>(W);
+    if (W.rules & TPC_RULE_GAP_MERGE) {
+        k_gap_back<<<grid, block, 0, s>>>(W);
+        k_gap_match<<<grid, block, 0, s>>>(W);
+        k_gap_link<<<grid, block, 0, s>>>(W);
+    }
     k_merge_match<<<grid, block, 0, s>>>(W);
     k_merge_link<<<grid, block, 0, s>>>(W);
     k_merge_heads<<<grid, block, 0, s>>>(W);

@@ -4,10 +4,11 @@
 //
 // One thread per track (the paper's one-thread-per-track mapping).  The seed is the circle
 // through the first, middle and last hit at the nominal calibration, so it does not depend on
-// theta; the fit runs from the last hit to the first.  The adjoint's forward pass stores the input
-// state of every step (coalesced by warp chunk) and the reverse sweep walks them backwards; a
-// low-memory form stores every K-th state (checkpoints) instead and recomputes each segment before
-// walking it backwards (same results, bit for bit).  Per-track chi2 and gradient contributions
+// theta; the fit runs from the last hit to the first.  The adjoint's forward pass stores every K-th
+// state (checkpoints) and the reverse sweep recomputes each segment's states from its checkpoint
+// before walking it backwards; a variant stores the input state of every step instead (coalesced
+// by warp chunk, 100 B per hit) and walks them backwards without recomputation (same results, bit
+// for bit).  Per-track chi2 and gradient contributions
 // (s_vd, and (d_k, a_k) for every sector the track visits) are written as records and summed in
 // FP64 in a fixed order (deterministic).
 #include "kf.cuh"
@@ -742,13 +743,13 @@ void launch_refit_grad_fit(const Work &W, const double *theta, const float *weig
     k_len_hist<<<W.sm_count * 4, 256, 0, s>>>(W, hist);
     k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
     k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
-    if (grad && W.tune.chunk[7] != 1) {     // every step's input state stored, no recomputation
+    if (grad && W.tune.chunk[7] == 1) {     // every step's input state stored, no recomputation
         k_chunk_len<<<W.sm_count * 4, 256, 0, s>>>(W, order, L);
         scan_exclusive(L.cl, L.cb, (int)(ck_tracks / 32 + 1), L.cn, L.cn + 1, W.scan_tmp, W.scan_tmp_len, s);
         k_refit_grad<3><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
         cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
         k_refit_grad<4><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
-    } else if (grad) {                      // checkpoints every CK_K steps, recomputation (less memory)
+    } else if (grad) {                      // checkpoints every CK_K steps, states recomputed (default)
         k_refit_grad<1><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);
         cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
         k_refit_grad<2><<<grid, block, 0, s>>>(W, theta, weight, anchor, model, L, rec, order);

@@ -32,6 +32,11 @@ struct tpc_ctx {
     static constexpr int kGraphs = 4;
     cudaGraphExec_t gexec[kGraphs];
     Work gwork[kGraphs];
+    bool ghasref[kGraphs];        // the graph also holds the refit / adjoint of the tracks
+    const double *gref_theta[kGraphs];
+    const float *gref_weight[kGraphs], *gref_anchor[kGraphs];
+    int32_t gref_model[kGraphs];
+    double *gref_sum[kGraphs], *gref_grad[kGraphs];
     bool gvalid[kGraphs];
     int gprofile[kGraphs];
     long long gused[kGraphs];
@@ -46,6 +51,7 @@ struct tpc_ctx {
     // launch shapes set by tpc_set_tuning (used when a call passes no tuning of its own)
     tpc_tuning tune;
     bool has_tune;
+    int32_t rules;            // TPC_RULE_* bits set by tpc_set_rules
 };
 
 namespace {
@@ -78,6 +84,7 @@ size_t layout(tpc_ctx *c, char *base) {
     const size_t npad = N + 8 * (nb + 2) + 64;
     const size_t C = (size_t)c->cap_chains + 1;
     Work &w = c->ws;
+    carve(cur, w.bin_ok, nb + 1);
     carve(cur, w.gyz, npad);
     carve(cur, w.gloc, npad);
     carve(cur, w.zoff, nb * ZOFF_STRIDE);
@@ -110,6 +117,9 @@ size_t layout(tpc_ctx *c, char *base) {
     carve(cur, w.trk_n, C + 1);
     carve(cur, w.trk_head, C);
     carve(cur, w.trk_pack, 2 * N);
+    carve(cur, w.gap_state, 6 * C);
+    carve(cur, w.gap_bestT, C);
+    carve(cur, w.gap_bestS, C);
     size_t scan_n = N > C ? N : C;
     scan_n = scan_n > nb ? scan_n : nb;
     const size_t scan_len = (size_t)scan_tmp_needed((int)scan_n) + 16;
@@ -148,12 +158,14 @@ Work make_work(const tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *o, co
     Work w = c->ws;
     w.pad = in->pad_fp;
     w.tim = in->time_fp;
-    w.bin_off = in->bin_off;
+    w.bin_off_in = in->bin_off;
+    w.bin_off = w.bin_ok;
     w.n_events = in->n_events;
     w.n_clusters = in->n_clusters;
     w.nbins = in->n_events * c->hgeom.n_sectors * c->hgeom.n_rows;
     w.ns = c->hgeom.n_sectors;
     w.nr = c->hgeom.n_rows;
+    w.rules = c->rules;
     w.geom = c->dgeom;
     w.sm_count = c->sm_count;
     w.label = o->label;
@@ -190,6 +202,7 @@ int enqueue_pipeline(const tpc_ctx *c, const Work &W, cudaStream_t s, bool captu
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_pipe[0], s, evf));
     TPC_CUDA(cudaMemsetAsync(W.counters, 0, 64 * sizeof(int32_t), s));
     if (W.n_clusters > 0) TPC_CUDA(cudaMemsetAsync(W.label, 0xff, (size_t)W.n_clusters * sizeof(int32_t), s));
+    launch_bins_check(W, s);
     launch_grid(W, s);
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_pipe[1], s, evf));
     launch_links(W, s);
@@ -205,6 +218,103 @@ int enqueue_pipeline(const tpc_ctx *c, const Work &W, cudaStream_t s, bool captu
     launch_refit(W, c->theta0, s);
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_pipe[7], s, evf));
     return cuda_err(cudaGetLastError());
+}
+
+// Arguments of the refit / adjoint part of a whole-step graph.
+struct RefitArgs {
+    const double *theta;
+    const float *weight, *anchor;
+    int32_t model;
+    double *sum, *grad;
+};
+
+// Refit under theta and its adjoint for the tracks counted in *n_tracks_dev (S0, S8, S9), enqueued
+// on s.  With profiling on, events between the refit stages (external event nodes when capturing).
+int enqueue_refit_grad(const tpc_ctx *c, const Work &W, const int32_t *n_tracks_dev, const double *theta,
+                       const float *weight, const float *anchor, int model, double *sum_chi2, double *grad,
+                       cudaStream_t s, bool capturing) {
+    const bool prof = c->profile != 0;
+    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[0], s, evf));
+    // the refit reads the track count from the workspace counters
+    TPC_CUDA(cudaMemcpyAsync(W.counters + CNT_NTRACKS, n_tracks_dev, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
+    launch_bins_check(W, s);
+    launch_pack_hits(W, s);
+    if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[1], s, evf));
+    launch_refit_grad_fit(W, theta, weight, anchor, model, grad != nullptr, c->ck, (long long)c->max_clusters + 1,
+                          (long long)c->cap_chains + 1, c->rec, c->order, c->lhist, s);
+    if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[2], s, evf));
+    launch_refit_grad_reduce(W, sum_chi2, grad, c->rec, c->part, s);
+    if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[3], s, evf));
+    return cuda_err(cudaGetLastError());
+}
+
+// The tracking pipeline (and, with ra, the refit / adjoint of its tracks) as one CUDA graph,
+// captured once per argument set and replayed; a few graphs are cached, least recently used first
+// out, and a recapture updates the executable graph in place when it can.
+int launch_graph(tpc_ctx *c, const Work &W, const RefitArgs *ra, cudaStream_t s) {
+    int slot = -1;
+    for (int k = 0; k < tpc_ctx::kGraphs; k++) {
+        if (!c->gvalid[k] || c->gprofile[k] != c->profile || c->ghasref[k] != (ra != nullptr) ||
+            std::memcmp(&W, &c->gwork[k], sizeof(Work)) != 0)
+            continue;
+        if (ra && (c->gref_theta[k] != ra->theta || c->gref_weight[k] != ra->weight ||
+                   c->gref_anchor[k] != ra->anchor || c->gref_model[k] != ra->model || c->gref_sum[k] != ra->sum ||
+                   c->gref_grad[k] != ra->grad))
+            continue;
+        slot = k;
+    }
+    if (slot < 0) {
+        slot = 0;   // an empty slot, else the least recently used
+        for (int k = 0; k < tpc_ctx::kGraphs; k++) {
+            if (!c->gvalid[k]) { slot = k; break; }
+            if (c->gused[k] < c->gused[slot]) slot = k;
+        }
+        cudaGraph_t graph = nullptr;
+        TPC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int erc = enqueue_pipeline(c, W, c->cap_stream, true);
+        if (erc == TPC_OK && ra)
+            erc = enqueue_refit_grad(c, W, W.n_tracks, ra->theta, ra->weight, ra->anchor, ra->model, ra->sum,
+                                     ra->grad, c->cap_stream, true);
+        const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (erc != TPC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return erc;
+        }
+        TPC_CUDA(ce);
+        if (c->gvalid[slot]) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(c->gexec[slot], graph, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->gexec[slot]);
+                c->gvalid[slot] = false;
+            }
+        }
+        if (!c->gvalid[slot]) {
+            const cudaError_t ie = cudaGraphInstantiate(&c->gexec[slot], graph, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return cuda_err(ie);
+            }
+        }
+        cudaGraphDestroy(graph);
+        c->gwork[slot] = W;
+        c->ghasref[slot] = ra != nullptr;
+        if (ra) {
+            c->gref_theta[slot] = ra->theta;
+            c->gref_weight[slot] = ra->weight;
+            c->gref_anchor[slot] = ra->anchor;
+            c->gref_model[slot] = ra->model;
+            c->gref_sum[slot] = ra->sum;
+            c->gref_grad[slot] = ra->grad;
+        }
+        c->gvalid[slot] = true;
+        c->gprofile[slot] = c->profile;
+    }
+    c->gused[slot] = ++c->gclock;
+    TPC_CUDA(cudaGraphLaunch(c->gexec[slot], s));
+    return TPC_OK;
 }
 
 }  // namespace
@@ -342,50 +452,9 @@ int tpc_track_batch(tpc_ctx *c, const tpc_clusters *in, tpc_tracks *out, const t
     if (rc) return rc;
     if ((rc = validate_out(out))) return rc;
     const Work W = make_work(c, in, out, tune);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int slot = -1;
-    for (int k = 0; k < tpc_ctx::kGraphs; k++)
-        if (c->gvalid[k] && c->gprofile[k] == c->profile && std::memcmp(&W, &c->gwork[k], sizeof(Work)) == 0)
-            slot = k;
-    if (slot < 0) {
-        slot = 0;   // an empty slot, else the least recently used
-        for (int k = 0; k < tpc_ctx::kGraphs; k++) {
-            if (!c->gvalid[k]) { slot = k; break; }
-            if (c->gused[k] < c->gused[slot]) slot = k;
-        }
-        cudaGraph_t graph = nullptr;
-        TPC_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        const int erc = enqueue_pipeline(c, W, c->cap_stream, true);
-        const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (erc != TPC_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return erc;
-        }
-        TPC_CUDA(ce);
-        if (c->gvalid[slot]) {
-            cudaGraphExecUpdateResultInfo info;
-            if (cudaGraphExecUpdate(c->gexec[slot], graph, &info) != cudaSuccess) {
-                cudaGetLastError();
-                cudaGraphExecDestroy(c->gexec[slot]);
-                c->gvalid[slot] = false;
-            }
-        }
-        if (!c->gvalid[slot]) {
-            const cudaError_t ie = cudaGraphInstantiate(&c->gexec[slot], graph, 0);
-            if (ie != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return cuda_err(ie);
-            }
-        }
-        cudaGraphDestroy(graph);
-        c->gwork[slot] = W;
-        c->gvalid[slot] = true;
-        c->gprofile[slot] = c->profile;
-    }
-    c->gused[slot] = ++c->gclock;
-    TPC_CUDA(cudaGraphLaunch(c->gexec[slot], s));
-    if (c->profile) c->pipe_pending = true;
-    return TPC_OK;
+    rc = launch_graph(c, W, nullptr, static_cast<cudaStream_t>(stream));
+    if (rc == TPC_OK && c->profile) c->pipe_pending = true;
+    return rc;
 }
 
 int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, const double *theta,
@@ -398,22 +467,44 @@ int tpc_refit_grad(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, co
     if (error_model != TPC_ERRORS_FIXED && error_model != TPC_ERRORS_RAW) return TPC_ERR_INVALID_ARG;
     int rc = validate_in(c, in);
     if (rc) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Work W = make_work(c, in, trk, nullptr);
-    // the refit reads the track count from the workspace counters
-    const bool prof = c->profile != 0;
-    if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[0], s));
-    TPC_CUDA(cudaMemcpyAsync(W.counters + CNT_NTRACKS, trk->n_tracks, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    launch_pack_hits(W, s);
-    if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[1], s));
-    launch_refit_grad_fit(W, theta, weight, anchor, error_model, grad != nullptr, c->ck, (long long)c->max_clusters + 1,
-                          (long long)c->cap_chains + 1, c->rec, c->order, c->lhist, s);
-    if (prof) TPC_CUDA(cudaEventRecord(c->ev_refit[2], s));
-    launch_refit_grad_reduce(W, sum_chi2, grad, c->rec, c->part, s);
-    if (prof) {
-        TPC_CUDA(cudaEventRecord(c->ev_refit[3], s));
-        c->refit_pending = true;
-    }
+    rc = enqueue_refit_grad(c, W, trk->n_tracks, theta, weight, anchor, error_model, sum_chi2, grad,
+                            static_cast<cudaStream_t>(stream), false);
+    if (rc == TPC_OK && c->profile) c->refit_pending = true;
+    return rc;
+}
+
+int tpc_track_refit_batch(tpc_ctx *c, const tpc_clusters *in, tpc_tracks *out, const double *theta,
+                          const float *weight, const float *anchor, int32_t error_model, double *sum_chi2,
+                          double *grad, const tpc_tuning *tune, void *stream) {
+    if (!c || !theta || !sum_chi2) return TPC_ERR_INVALID_ARG;
+    if (anchor && (reinterpret_cast<uintptr_t>(anchor) & 15u)) return TPC_ERR_INVALID_ARG;
+    if (error_model != TPC_ERRORS_FIXED && error_model != TPC_ERRORS_RAW) return TPC_ERR_INVALID_ARG;
+    int rc = validate_in(c, in);
+    if (rc) return rc;
+    if ((rc = validate_out(out))) return rc;
+    const Work W = make_work(c, in, out, tune);
+    const RefitArgs ra{theta, weight, anchor, error_model, sum_chi2, grad};
+    rc = launch_graph(c, W, &ra, static_cast<cudaStream_t>(stream));
+    if (rc == TPC_OK && c->profile) c->pipe_pending = c->refit_pending = true;
+    return rc;
+}
+
+int tpc_its_match(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, const float *its, int32_t n_its,
+                  int32_t *match_trk, int32_t *match_its, float *anchor, void *stream) {
+    if (!c || !trk || !trk->trk_off || !trk->trk_hits || !trk->par || !trk->cov || !trk->xref || !trk->ndf ||
+        !trk->n_tracks || trk->cap_tracks < 1 || !match_trk || n_its < 0 || (n_its > 0 && (!its || !match_its)))
+        return TPC_ERR_INVALID_ARG;
+    if (anchor && (reinterpret_cast<uintptr_t>(anchor) & 15u)) return TPC_ERR_INVALID_ARG;
+    int rc = validate_in(c, in);
+    if (rc) return rc;
+    if (n_its > c->cap_chains || its_match_nphi() > c->nbins_max) return TPC_ERR_CAPACITY;
+    const Work W = make_work(c, in, trk, nullptr);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
+    launch_bins_check(W, s);
+    const double ha = c->geom.half_angle_deg * M_PI / 180.0;
+    launch_its_match(W, its, n_its, match_trk, match_its, anchor, -0.299792458e-2 * c->bz, ha, 2.0 * ha, s);
     return cuda_err(cudaGetLastError());
 }
 
@@ -434,7 +525,10 @@ int tpc_merge_slices(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *slice
     W.s_ev_trk_off = slice_trk->ev_trk_off;
     W.s_n_tracks = slice_trk->n_tracks;
     W.slice_len = slice_len;
-    launch_frame_merge(W, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
+    launch_bins_check(W, s);
+    launch_frame_merge(W, s);
     return cuda_err(cudaGetLastError());
 }
 
@@ -476,6 +570,19 @@ int tpc_profile_read(tpc_ctx *c, double *ms, int32_t cap, int32_t *n_calls) {
         for (int i = 0; i < n; i++) c->acc_ms[i] = 0.0;
         c->acc_calls = 0;
     }
+    return n;
+}
+
+int tpc_set_rules(tpc_ctx *c, int32_t rules) {
+    if (!c || (rules & ~(TPC_RULE_SKIP_ROW | TPC_RULE_GAP_MERGE))) return TPC_ERR_INVALID_ARG;
+    c->rules = rules;
+    return TPC_OK;
+}
+
+int tpc_rule_constants(int64_t *out, int32_t cap) {
+    const int64_t v[] = {TPC_RULE_SKIP_ROW, TPC_RULE_GAP_MERGE, GAP_MAX};
+    const int n = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < n && i < cap; i++) out[i] = v[i];
     return n;
 }
 

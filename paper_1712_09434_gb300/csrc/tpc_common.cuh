@@ -23,6 +23,7 @@ constexpr int N_MIN = 10;         // minimum kept hits of an accepted segment
 constexpr int W_MERGE = 192;      // merge window |dY|, |dZ| (LSB)
 constexpr int MERGE_XMAX = 2048;  // maximum merge extrapolation distance (LSB)
 constexpr int MERGE_BACK = 3;     // direction baseline of a segment end (hits)
+constexpr int GAP_MAX = 24;       // gap merge: largest row distance between the two segment ends
 
 constexpr int MAX_ROWS = 512;
 constexpr int MAX_SECTORS = 64;
@@ -69,15 +70,20 @@ struct Work {
     // inputs
     const int16_t *pad;
     const uint16_t *tim;
-    const int32_t *bin_off;
+    const int32_t *bin_off;   // the checked copy of the bin offsets (bin_ok) that every stage reads
+    const int32_t *bin_off_in;  // the caller's bin offsets, read only by the check
     int n_events, n_clusters, nbins;
     int ns, nr;               // sectors, rows (host copies of the geometry)
+    int rules;                // TPC_RULE_* bits (0: the plain readings)
     // outputs
     int32_t *label, *trk_off, *trk_hits, *ev_trk_off, *ndf, *n_tracks;
     float *par, *xref, *cov, *chi2;
     int cap_tracks, cap_hits;
     // geometry
     const DevGeom *geom;
+    // workspace: checked bin offsets [nbins + 1]: the caller's, or (if any offset is out of range
+    // or decreasing, or the offsets do not run from 0 to n_clusters) every cluster in the last bin
+    int32_t *bin_ok;
     // workspace: grid (S1)
     int32_t *gyz;             // [npad] packed (Y & 0xffff) | (Z << 16), slab order
     uint16_t *gloc;           // [npad] row-local cluster index, slab order
@@ -112,6 +118,9 @@ struct Work {
     int32_t *trk_n;           // [cap_tracks + 1] hits per track, then exclusive scan
     int32_t *trk_head;        // [cap_tracks] head segment of each track
     int32_t *trk_pack;        // [cap_hits * 2] (Y | Z<<16, sector | row<<16) per hit
+    // gap merge (TPC_RULE_GAP_MERGE)
+    long long *gap_state;     // [cap_chains * 6] backward filter state (p, v, a of Y and Z) at the first kept hit
+    unsigned long long *gap_bestT, *gap_bestS;  // [cap_chains] (D << 32 | index)
     // time-frame slice merge (S11): the per-slice tracks it reads (device)
     const int32_t *s_trk_off, *s_trk_hits, *s_ev_trk_off, *s_n_tracks;
     int slice_len;
@@ -133,6 +142,7 @@ enum {
     CNT_FRAME_N = 4,          // slice merge: slice tracks read, frame tracks, frame hits
     CNT_FRAME_T = 5,
     CNT_FRAME_H = 6,
+    CNT_BINS_BAD = 7,         // set when the caller's bin offsets fail the check
     CNT_Q0 = 8,               // work-queue heads, one per kernel
 };
 
@@ -176,6 +186,7 @@ __device__ __forceinline__ int queue_next(int32_t *head, int chunk, int *sh) {
 #endif
 
 // ---- launchers (host side, one per translation unit) ----------------------------------------
+void launch_bins_check(const Work &W, cudaStream_t s);
 void launch_grid(const Work &W, cudaStream_t s);
 void launch_links(const Work &W, cudaStream_t s);
 void launch_chains(const Work &W, cudaStream_t s);
@@ -193,6 +204,9 @@ size_t refit_ck_words(long long cap_hits, long long cap_tracks);
 int refit_rec_words(int cap_tracks);
 int refit_part_doubles(int cap_tracks, int ns);
 void launch_pack_hits(const Work &W, cudaStream_t s);
+void launch_its_match(const Work &W, const float *its, int n_its, int32_t *match_trk, int32_t *match_its,
+                      float *anchor, double kB, double alpha0, double dalpha, cudaStream_t s);
+int its_match_nphi();
 void prepare_kernels();
 // device-wide exclusive scan of n (host) or *n_dev (device, if not NULL) int32 values; writes
 // out[0..n] (out[n] = total) and *total_dev (if not NULL).

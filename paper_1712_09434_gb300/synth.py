@@ -423,6 +423,52 @@ def vertex_references(ev: Event, trk_off, trk_hits, seed=1006, purity=0.9, smear
     return out
 
 
+# ITS-like reference tracks (the inner tracker's tracks, matched to TPC tracks for the drift
+# calibration, sections 2.1 and 6 of the paper): resolution of the direction at the vertex, of z0,
+# tan lambda and q/pT, efficiency per particle, and the fraction of fake tracks
+ITS_SIGMA_PHI = 1e-3
+ITS_SIGMA_Z0 = 0.01
+ITS_SIGMA_TL = 1e-3
+ITS_SIGMA_QPT_REL = 0.01
+ITS_EFF = 0.95
+ITS_FAKE_FRAC = 0.02
+
+
+def its_tracks(ev: Event, seed=1007, eff=ITS_EFF, fake_frac=ITS_FAKE_FRAC, smear=True):
+    """Reference tracks of the inner tracker for the particles of ev, as float64 [n_its, 8]:
+    (phi0, z0, tan lambda, q/pT, sigma_phi0, sigma_z0, sigma_tl, sigma_qpt) at the production vertex
+    (global azimuth of the momentum, z at the vertex, exactly 0 for a true track).  Each particle
+    gives a track with probability `eff`, smeared with seeded Gaussian noise (exact if smear is
+    False); fake tracks, a `fake_frac` share, take the kinematics of random particles with a random
+    azimuth and z0 ~ N(0, 5 cm).  Returns (tracks, particle index or -1 for fakes).  The rows come
+    in a random order (no relation to the particle order)."""
+    rng = np.random.default_rng(seed)
+    npart = len(ev.trk_pt)
+    keep = np.nonzero(rng.random(npart) < eff)[0]
+    n_fake = int(round(fake_frac * keep.size))
+    noise = rng.normal(0.0, 1.0, size=(keep.size, 4)) if smear else np.zeros((keep.size, 4))
+    tl = np.sinh(ev.trk_eta[keep])
+    qpt = ev.trk_q[keep] / ev.trk_pt[keep]
+    sq = ITS_SIGMA_QPT_REL * np.abs(qpt)
+    rec = np.stack([np.mod(ev.trk_phi0[keep] + ITS_SIGMA_PHI * noise[:, 0], 2 * math.pi),
+                    ITS_SIGMA_Z0 * noise[:, 1], tl + ITS_SIGMA_TL * noise[:, 2], qpt + sq * noise[:, 3],
+                    np.full(keep.size, ITS_SIGMA_PHI), np.full(keep.size, ITS_SIGMA_Z0),
+                    np.full(keep.size, ITS_SIGMA_TL), sq], axis=1)
+    if n_fake and npart:
+        src = rng.integers(0, npart, n_fake)
+        ftl = np.sinh(ev.trk_eta[src])
+        fq = ev.trk_q[src] / ev.trk_pt[src]
+        fake = np.stack([rng.uniform(0.0, 2 * math.pi, n_fake), rng.normal(0.0, 5.0, n_fake), ftl, fq,
+                         np.full(n_fake, ITS_SIGMA_PHI), np.full(n_fake, ITS_SIGMA_Z0),
+                         np.full(n_fake, ITS_SIGMA_TL), ITS_SIGMA_QPT_REL * np.abs(fq)], axis=1)
+        rec = np.concatenate([rec, fake])
+        part = np.concatenate([keep, np.full(n_fake, -1)])
+    else:
+        part = keep
+    o = rng.permutation(rec.shape[0])
+    return rec[o], part[o].astype(np.int64)
+
+
 @dataclasses.dataclass
 class Batch:
     pad_fp: np.ndarray

@@ -29,7 +29,7 @@ CANDIDATES = {
     "select": dict(block=[256, 512, 1024], ctas=[1, 2, 4], chunk=[0]),
     "merge": dict(block=[64, 128, 256, 512], ctas=[4, 8, 16], chunk=[0]),
     "refit": dict(block=[64, 128], ctas=[2, 4, 8, 16], chunk=[0]),
-    "refit_grad": dict(block=[64, 128], ctas=[2, 4, 8], chunk=[0]),     # 0: stored states (1: checkpoints)
+    "refit_grad": dict(block=[64, 128], ctas=[2, 4, 8], chunk=[0, 1]),  # 0: checkpoints, 1: stored states
 }
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 

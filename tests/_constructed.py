@@ -130,3 +130,58 @@ def edge_events():
         b.add(s, R, 100 + 5 * R, min(max(zR, 0), 32001))
     flush()
     return [e.build() for e in events]
+
+
+def rule_events():
+    """Events for the rules on inefficient data, one construction per sector: straight tracks with
+    single empty rows (links across them) and with the partner across the empty row displaced to
+    the edge of the scaled cut; two pieces of a track separated by 7 to 25 empty rows; the second
+    piece shifted parallel by the gap radius and one LSB more; a second piece of a steeper slope;
+    a piece whose extrapolation leaves the sector inside the gap."""
+    events = []
+    b = Builder()
+    sec = iter(range(N_SECTORS))
+
+    def next_sector():
+        nonlocal b, sec
+        try:
+            return next(sec)
+        except StopIteration:
+            events.append(b)
+            b = Builder()
+            sec = iter(range(N_SECTORS))
+            return next(sec)
+
+    for missing in ([40], [40, 60], [40, 42], [40, 41]):
+        s = next_sector()
+        b.line(s, [r for r in range(20, 90) if r not in missing], -300, 11, 6000, 25)
+    # the partner across an empty row displaced: residual limits 178 (one side skips) and 116
+    # (both sides skip, displacement on the up partner)
+    for both, delta in ((False, 178), (False, 179), (True, 116), (True, 117)):
+        s = next_sector()
+        rows = [r for r in range(20, 60) if r not in ((39, 41) if both else (41,))]
+        for r in rows:
+            b.add(s, r, -300 + 11 * r + (delta if r == 42 else 0), 6000 + 25 * r)
+    for gap in (7, 8, 12, 23, 24, 25):
+        s = next_sector()
+        b.line(s, range(30, 60), -300, 9, 7000, 30)
+        b.line(s, range(60 + gap, min(60 + gap + 30, N_ROWS)), -300, 9, 7000, 30)
+    for gap in (8, 12):
+        w = 77 + 38 * gap
+        for delta in (w, w + 1, -w, -w - 1):
+            s = next_sector()
+            b.line(s, range(30, 60), -300, 9, 7000, 30)
+            for r in range(60 + gap, 60 + gap + 30):
+                b.add(s, r, -300 + 9 * r + delta, 7000 + 30 * r)
+    s = next_sector()
+    b.line(s, range(30, 60), -300, 9, 7000, 30)
+    for r in range(72, 100):
+        b.add(s, r, -300 + 9 * 72 + 69 * (r - 72), 7000 + 30 * r)
+    s = next_sector()
+    y_end = ymax(66) - 6 * 90
+    for r in range(30, 60):
+        b.add(s, r, y_end - 90 * (59 - r), 7000 + 30 * r)
+    for r in range(72, 92):
+        b.add(s, r, min(y_end + 90 * (r - 59), ymax(r)), 7000 + 30 * r)
+    events.append(b)
+    return [e.build() for e in events]

@@ -17,7 +17,7 @@ def fake_result():
         "n_tracks": 218_000, "n_hits": 26_000_000, "weighted_hits": 25_000_000, "n_chains": 790_000,
         "cand_hits": 68_000_000, "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5},
         "tuning": {"key": "k", "source": "cache"}, "prof": ({k: v * n_calls for k, v in ms.items()}, n_calls),
-        "ms_plain": 114.0, "ms_grad_event": 1.0, "n_tracks_c5": 25_779, "calib": {}, "single": {},
+        "ms_plain": 114.0, "ms_grad_event": 1.2, "ms_grad_event_stored": 1.0, "n_tracks_c5": 25_779, "calib": {}, "single": {},
         "frame": {"value": 1.5e9}, "h2d": 134_324_888, "d2h": 365_388_892, "ms_e2e": 12.7, "ms_e2e_seq": 15.4,
     }
 
@@ -41,9 +41,17 @@ def test_bench_line_has_every_contract_key_and_consistent_figures():
     assert "traffic" in r
     e = line["e2e"]
     assert e["value"] == pytest.approx(33e6 / 12.7e-3) and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
-    assert line["gpu_launches"] == bench.LAUNCHES_PER_STEP * 40
+    # no tuned shapes: the library default adjoint (states recomputed from checkpoints)
+    assert line["adjoint_form_in_step"] == "checkpoints"
+    assert line["gpu_launches"] == (bench.LAUNCHES_TRACKING + bench.LAUNCHES_REFIT_GRAD["checkpoints"]) * 40
     assert line["stage_tflops"]["refit_grad"] == pytest.approx(
-        (bench.FLOP_FWD + bench.FLOP_ADJ) * 25e6 / 2.2e-3 / 1e12)
+        (2 * bench.FLOP_FWD + bench.FLOP_ADJ) * 25e6 / 2.2e-3 / 1e12)
+    # with the stored-state form tuned in: fewer flop per hit, four more launches
+    res2 = fake_result()
+    res2["tuning"] = {"key": "k", "source": "cache", "best": {"refit_grad": [64, 8, 1]}}
+    line2 = bench.finish_native(args, res2, 1)
+    assert line2["gpu_launches"] == (bench.LAUNCHES_TRACKING + bench.LAUNCHES_REFIT_GRAD["stored states"]) * 40
+    assert line2["stage_tflops"]["refit_grad"] == pytest.approx((bench.FLOP_FWD + bench.FLOP_ADJ) * 25e6 / 2.2e-3 / 1e12)
 
 
 def test_alu_roofline_when_the_gradient_stage_dominates():
@@ -56,3 +64,7 @@ def test_alu_roofline_when_the_gradient_stage_dominates():
     r = bench.finish_native(args, res, 1)["roofline"]
     assert r["bound"] == "alu" and r["kernel"] == "refit_grad" and r["unit"] == "TFLOP/s"
     assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS)
+    # a measured FMA peak replaces the derived one
+    res["fp32_peak"] = {"tflops": 70.0, "config": "c", "clocks": None}
+    r = bench.finish_native(args, res, 1)["roofline"]
+    assert r["peak"] == 70.0 and r["frac"] == pytest.approx(r["achieved"] / 70.0) and "measured" in r["peak_kind"]

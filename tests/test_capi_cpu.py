@@ -39,6 +39,13 @@ def test_constants_match_oracle(lib_path):
     assert mine == list(O.constants().values())
 
 
+def test_rule_constants_match_oracle(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    buf = (ctypes.c_int64 * 8)()
+    n = lib.tpc_rule_constants(buf, 8)
+    assert [buf[i] for i in range(n)] == list(O.rule_constants().values())
+
+
 def test_strerror_covers_codes(lib_path):
     lib = ctypes.CDLL(lib_path)
     lib.tpc_strerror.restype = ctypes.c_char_p

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_1712_09434_gb300 import capi
+from paper_1712_09434_gb300 import capi, synth
 from tests import _events, _gpu
 
 pytestmark = pytest.mark.gpu
@@ -97,7 +97,6 @@ def test_slice_merge_arguments_and_capacity():
     """tpc_merge_slices: slice lengths outside [1, 32001] and missing outputs are invalid; a frame
     output too small for the frame tracks is a capacity error on the device, with nothing written
     beyond it."""
-    from paper_1712_09434_gb300 import synth
     tf = synth.time_frame([_events.event("c1")], t0=[0], slice_len=16000)
     ctx = _gpu.make_context(tf.n_clusters, tf.n_slices)
     cl = capi.Clusters.from_numpy(tf.pad_fp, tf.time_fp, tf.bin_off, tf.n_slices)
@@ -123,4 +122,54 @@ def test_slice_merge_arguments_and_capacity():
     ctx.tpc_merge_slices(cl, st, tf.slice_len, fr)
     assert ctx.tpc_sync_status() == capi.TPC_OK
     assert int(fr.n_tracks.item()) > 50
+    ctx.close()
+
+
+def _bad_offsets(n, nbins, kind):
+    """Bin offsets that break the layout rule 0 = bo[0] <= ... <= bo[nbins] = n."""
+    bo = np.linspace(0, n, nbins + 1).astype(np.int64)
+    if kind == "past_end":          # the offsets run past the clusters (a write past the grid)
+        bo = np.linspace(0, 5 * n, nbins + 1).astype(np.int64)
+    elif kind == "decreasing":
+        bo[nbins // 2] = bo[nbins // 2 - 1] - 3
+    elif kind == "short":           # clusters after the last bin
+        bo[-1] = n - 100
+    elif kind == "negative":
+        bo[1] = -50
+    return bo.astype(np.int32)
+
+
+@pytest.mark.parametrize("kind", ["past_end", "decreasing", "short", "negative"])
+def test_malformed_bin_offsets_are_a_bounds_error_with_nothing_written_outside(kind):
+    """Bin offsets outside [0, n_clusters], decreasing, or not ending at n_clusters: every call
+    reports TPC_ERR_BOUNDS, finds no track, leaves the bytes after its outputs untouched, and the
+    context works normally afterwards."""
+    ev = _events.event("c1")
+    n, nbins = ev.n_clusters, 36 * 159
+    ctx = _gpu.make_context(n, 1)
+    bad = capi.Clusters.from_numpy(ev.pad_fp, ev.time_fp, _bad_offsets(n, nbins, kind), 1)
+    tail = 4096
+    for batch in (False, True):
+        tr = capi.Tracks(n, 1, 1024, n)
+        outer = {}
+        for name, m, dt in [("label", n, torch.int32), ("trk_off", 1025, torch.int32), ("trk_hits", n, torch.int32)]:
+            big = torch.full((m + tail,), 12345, dtype=dt, device="cuda")
+            setattr(tr, name, big[:m])
+            outer[name] = (big, m)
+        if batch:
+            ctx.tpc_track_batch(bad, tr)
+        else:
+            ctx.tpc_track_event(bad, tr)
+        assert ctx.tpc_sync_status() == capi.TPC_ERR_BOUNDS
+        assert int(tr.n_tracks.item()) == 0
+        assert bool((tr.label == -1).all())
+        for name, (big, m) in outer.items():
+            assert bool((big[m:] == 12345).all()), name
+    good = _gpu.run(ctx, _gpu.clusters_of(ev))
+    assert good["n_tracks"] > 50
+    # the refit of those tracks against the malformed offsets: also a bounds error
+    s = torch.empty(1, dtype=torch.float64, device="cuda")
+    th = torch.tensor(synth.theta_nominal(), dtype=torch.float64, device="cuda")
+    ctx.tpc_refit_grad(bad, good["tracks_obj"], th, s, None)
+    assert ctx.tpc_sync_status() == capi.TPC_ERR_BOUNDS
     ctx.close()

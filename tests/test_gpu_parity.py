@@ -3,8 +3,9 @@
 Integer steps (S2 links, S3/S4 chains, S5 candidates, S6 selection, S7 merge, final hit lists and
 labels) must be bit-exact.  The FP32 refit (S8) must agree with the FP64 oracle to 1e-4 relative,
 measured against max(|p|, unit, sigma_p) with units (1 cm, 1 cm, 0.1, 0.1, 0.1 c/GeV) because y,
-sin phi, tan lambda and q/pT cross zero, and sigma_p the oracle's statistical error; the adjoint gradient (S9) must agree with FP64 central differences
-of the oracle to 1e-3 in norm per parameter block (s_vd, d_k, a_k).  The oracle always runs on its own
+sin phi, tan lambda and q/pT cross zero, and sigma_p the oracle's statistical error; the adjoint
+gradient (S9) must agree with FP64 central differences of the oracle to 1e-3 per component, relative
+to max(|g_i|, 1e-3 max |g|), and to 1e-3 in norm per parameter block (s_vd, d_k, a_k).  The oracle always runs on its own
 track lists (the GPU's are first checked equal to them) and never on a CUDA output.
 """
 import numpy as np
@@ -140,8 +141,27 @@ def _refit_sum_grad(ctx, cl, tr, theta, w, ref=None, model=0):
 
 
 def _grad_err(g, ref):
+    """Per-component error relative to max(|g_i|, 1e-3 max_j |g_j|): components near zero (at the
+    optimum every component is a sum of cancelling contributions) are held on the scale of the
+    largest one."""
     floor = 1e-3 * np.abs(ref).max()
     return np.abs(g - ref) / np.maximum(np.abs(ref), floor)
+
+
+FD_STEPS = (1e-6, 1e-4, 1e-4)
+
+
+def _fd_reference(ev, o, theta, w, ref, model):
+    """The oracle's FP64 central differences at the steps h and h/2: their per-component difference
+    (truncation and cancellation error of the reference) must stay below 1e-4 on the scale of
+    _grad_err, ten times under the tolerance the GPU gradient is held to."""
+    args = (ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta)
+    g_h = O.grad_fd(*args, h=FD_STEPS, weight=w, ref=ref, mode=model)
+    g_h2 = O.grad_fd(*args, h=tuple(x / 2 for x in FD_STEPS), weight=w, ref=ref, mode=model)
+    noise = _grad_err(g_h2, g_h).max()
+    print("FD reference noise (h vs h/2, per component) %.2e" % noise)
+    assert noise < 1e-4, noise
+    return g_h
 
 
 def _block_err(g, ref, ns=36):
@@ -178,14 +198,40 @@ def test_adjoint_gradient_matches_fp64_central_differences(ctx, which):
     s_gpu, g_gpu = _refit_sum_grad(ctx, cl, g["tracks_obj"], theta, w, ref, model)
     s_ref = O.chi2_total(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w, ref=ref,
                          mode=model)
-    g_ref = O.grad_fd(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w, ref=ref,
-                      mode=model)
+    g_ref = _fd_reference(ev, o, theta, w, ref, model)
     print("sum chi2 gpu %.6f oracle %.6f (%d of %d tracks)" % (s_gpu, s_ref, int(w.sum()), len(w)))
     assert s_gpu == pytest.approx(s_ref, rel=1e-4)
     err = _grad_err(g_gpu, g_ref)
     blk = _block_err(g_gpu, g_ref)
     print("grad block rel err (s, d, a) %s; max component rel err %.3e" % (blk, err.max()))
+    assert err.max() < GRAD_RTOL, (err.argmax(), err.max())
     assert np.all(blk < GRAD_RTOL), blk
+
+
+def test_adjoint_gradient_at_calibration_event_size(ctx):
+    """The calibration objective of the 20,000-track event (raw errors, vertex references, tracks
+    of nominal chi2/ndf < 5) at the nominal calibration: every component within 1e-3 of the oracle's
+    FP64 central differences.  (At the injected calibration the objective's curvature along s_vd and
+    the d_k, ~2e12 here, turns FP32 noise of a few 1e-9 in those coordinates into gradient errors
+    above 1e-3 of the largest component; the 3000-track case above holds every component to 1e-3
+    there, and the measured errors of the full event are stated with the tolerances.)"""
+    ev = _events.event("c5")
+    o = O.track_event(ev.pad_fp, ev.time_fp, ev.bin_off)
+    w = _weights(O.fit(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"]))
+    cl = _gpu.clusters_of(ev)
+    g = _gpu.run(ctx, cl)
+    _compare_tracks(g, o, ev.n_clusters)
+    ref = synth.vertex_references(ev, o["trk_off"], o["trk_hits"]).astype(np.float32).astype(np.float64)
+    theta = synth.theta_nominal()
+    s_gpu, g_gpu = _refit_sum_grad(ctx, cl, g["tracks_obj"], theta, w, ref, 1)
+    s_ref = O.chi2_total(ev.pad_fp, ev.time_fp, ev.bin_off, o["trk_off"], o["trk_hits"], theta, weight=w, ref=ref,
+                         mode=1)
+    g_ref = _fd_reference(ev, o, theta, w, ref, 1)
+    err = _grad_err(g_gpu, g_ref)
+    print("C5 nominal: sum chi2 gpu %.6f oracle %.6f; max component rel err %.3e at %d; blocks %s" % (
+        s_gpu, s_ref, err.max(), err.argmax(), _block_err(g_gpu, g_ref)))
+    assert s_gpu == pytest.approx(s_ref, rel=1e-4)
+    assert err.max() < GRAD_RTOL, (err.argmax(), err.max())
 
 
 def test_calib_refit_autograd_function(ctx):
@@ -279,8 +325,8 @@ def test_launch_shapes_do_not_change_results(ctx):
               "select": (256, 1, 0), "merge": (512, 4, 0), "refit": (64, 2, 0), "refit_grad": (64, 2, 0)}
     staged = dict(shapes, links=(128, 8, 1))        # neighbour rows staged in shared memory
     slab = dict(shapes, links=(96, 16, 2))          # lanes in cluster order (default: Z-slab order)
-    ckpt = dict(shapes, refit_grad=(128, 4, 1))     # gradient from checkpoints (default: stored states)
-    for sh in (shapes, staged, slab, ckpt):
+    stored = dict(shapes, refit_grad=(128, 4, 1))   # gradient from stored states (default: checkpoints)
+    for sh in (shapes, staged, slab, stored):
         ctx.tpc_set_tuning(tune.to_struct(sh))
         try:
             g1, s1, gr1 = run_all()
@@ -313,3 +359,34 @@ def test_stage_profile_reports_every_stage(ctx):
     assert list(ms) == capi.STAGES
     assert all(v > 0.0 for v in ms.values()), ms
     assert sum(ms.values()) < 1000.0
+
+
+def test_whole_step_graph_equals_the_two_calls(ctx):
+    """tpc_track_refit_batch (tracking and refit / adjoint captured as one graph) gives the tracks,
+    sum of chi2 and gradient of tpc_track_batch followed by tpc_refit_grad, bit for bit, on its
+    first call (capture) and on a replay."""
+    from paper_1712_09434_gb300 import capi
+    cfgs = synth.batch_configs(n_events=5, seed0=2400)
+    for c in cfgs:
+        c.n_tracks = min(c.n_tracks, 2500)
+    b = synth.concat_events([synth.make_event(c) for c in cfgs])
+    cl = _gpu.clusters_of(b, b.n_events)
+    th = torch.tensor(synth.theta_nominal(), dtype=torch.float64, device="cuda")
+    g0 = _gpu.run(ctx, cl, n_events=b.n_events, batch=True)
+    s0 = torch.empty(1, dtype=torch.float64, device="cuda")
+    gr0 = torch.empty(73, dtype=torch.float64, device="cuda")
+    ctx.tpc_refit_grad(cl, g0["tracks_obj"], th, s0, gr0)
+    assert ctx.tpc_sync_status() == 0
+    n = cl.n_clusters
+    tr = capi.Tracks(n, b.n_events, max(n // 10 + 16, 64), n)
+    s1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    gr1 = torch.empty(73, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        s1.fill_(0.0)
+        gr1.fill_(0.0)
+        ctx.tpc_track_refit_batch(cl, tr, th, s1, gr1)
+        assert ctx.tpc_sync_status() == 0
+        h = tr.to_host()
+        for k in ("trk_off", "trk_hits", "label", "par", "cov", "chi2", "ndf"):
+            np.testing.assert_array_equal(h[k], g0[k], err_msg=k)
+        assert torch.equal(s1, s0) and torch.equal(gr1, gr0)

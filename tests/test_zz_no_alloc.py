@@ -60,3 +60,26 @@ def test_noalloc_rejects_inputs_beyond_the_static_scratch():
     cb = _gpu.clusters_of(batch, 3)
     rc = capi.tpc_links_noalloc(capi.default_geometry(), cb, up, up)
     assert rc == capi.TPC_ERR_CAPACITY
+
+
+def test_noalloc_malformed_bin_offsets_are_a_bounds_error():
+    """Offsets running past the clusters would index past the static scratch: the call reports
+    TPC_ERR_BOUNDS in its status word, makes no link, and the next call works normally."""
+    ev = _events.event("c1")
+    n, nbins = ev.n_clusters, 36 * 159
+    bo = np.linspace(0, 5 * n, nbins + 1).astype(np.int32)
+    cl = capi.Clusters.from_numpy(ev.pad_fp, ev.time_fp, bo, 1)
+    tail = 1024
+    up = torch.full((n + tail,), -7, dtype=torch.int32, device="cuda")
+    down = torch.full((n + tail,), -7, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = capi.tpc_links_noalloc(capi.default_geometry(), cl, up[:n], down[:n], status)
+    assert rc == capi.TPC_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) & 4                        # the library's bounds bit
+    assert bool((up[:n] == -1).all()) and bool((down[:n] == -1).all())
+    assert bool((up[n:] == -7).all()) and bool((down[n:] == -7).all())
+    ref_up, ref_down = _reference_links(ev)
+    up2, down2 = _noalloc_links(ev)
+    np.testing.assert_array_equal(up2, ref_up)
+    np.testing.assert_array_equal(down2, ref_down)
