@@ -107,12 +107,13 @@ __device__ int extend(const Work &W, const DevGeom &g, Abg &fy, Abg &fz, int row
 }
 
 // Each warp takes 32 x chunk chains at a time from the queue (no CTA barrier: a warp whose chains
-// end early takes the next ones while the others still follow theirs).
+// end early takes the next ones while the others still follow theirs).  SKIP: chains may skip a
+// row (the skip-row rule); the plain instantiation keeps the plain reading's registers.
+template <bool SKIP>
 __global__ void __launch_bounds__(128) k_follow(Work W) {
     const DevGeom &g = *W.geom;
     const int nr = g.n_rows;
     const int lane = threadIdx.x & 31;
-    const bool skip = (W.rules & TPC_RULE_SKIP_ROW) != 0;
     int n_chains = W.counters[CNT_NCHAINS];
     if (n_chains > W.cap_chains) n_chains = W.cap_chains;
     const int chunk = 32 * (W.tune.chunk[3] > 0 ? W.tune.chunk[3] : 1);
@@ -127,46 +128,82 @@ __global__ void __launch_bounds__(128) k_follow(Work W) {
             const int row0 = bin % nr;
             const int rowbase = bin - row0;
             int32_t *slots = W.cand_slots + (size_t)t * nr;
-            // filter along the chain in ascending rows, writing the chain hits (one filter step per
-            // pad row: a row skipped by a link is a prediction without an update and a -1 slot)
             Abg fy, fz;
-            int x = start, m0y = 0, m0z = 0, row = row0, rprev = row0;
-            for (int k = 0; k < len; k++) {
-                const int y = __ldg(W.pad + x), z = __ldg(W.tim + x);
-                slots[row] = x;
-                const int d = row - rprev;
-                if (k == 0) {
-                    m0y = y;
-                    m0z = z;
-                } else {
-                    if (k == 1) {   // state at the first hit with the velocity of the step to the second
-                        abg_init(fy, m0y, y, d);
-                        abg_init(fz, m0z, z, d);
-                    }
-                    for (int j = 0; j < d; j++) {
+            int row_last;
+            if constexpr (!SKIP) {
+                // filter along the chain in ascending rows (consecutive rows), writing the chain hits
+                int x = start, m0y = 0, m0z = 0;
+                for (int k = 0; k < len; k++) {
+                    const int y = __ldg(W.pad + x), z = __ldg(W.tim + x);
+                    slots[row0 + k] = x;
+                    if (k == 0) {
+                        m0y = y;
+                        m0z = z;
+                    } else {
+                        if (k == 1) {   // state at the first hit with velocity m1 - m0
+                            abg_init(fy, m0y, y, 1);
+                            abg_init(fz, m0z, z, 1);
+                        }
                         abg_predict(fy);
                         abg_predict(fz);
+                        abg_update(fy, y);
+                        abg_update(fz, z);
                     }
-                    abg_update(fy, y);
-                    abg_update(fz, z);
+                    if (k + 1 < len) x = W.up[x];
                 }
-                rprev = row;
-                if (k + 1 < len) {
-                    x = W.up[x];
-                    // the next hit is one row further, or two across a row the link skips
-                    if (skip && row + 2 < nr && x >= __ldg(W.bin_off + rowbase + row + 2)) {
-                        slots[row + 1] = -1;
-                        row += 2;
+                row_last = row0 + len - 1;
+            } else {
+                // the same with links that may skip a row: one filter step per pad row, a skipped
+                // row is a prediction without an update and a -1 slot
+                int x = start, m0y = 0, m0z = 0, row = row0, rprev = row0;
+                for (int k = 0; k < len; k++) {
+                    const int y = __ldg(W.pad + x), z = __ldg(W.tim + x);
+                    slots[row] = x;
+                    const int d = row - rprev;
+                    if (k == 0) {
+                        m0y = y;
+                        m0z = z;
                     } else {
-                        row += 1;
+                        if (k == 1) {
+                            abg_init(fy, m0y, y, d);
+                            abg_init(fz, m0z, z, d);
+                        }
+                        for (int j = 0; j < d; j++) {
+                            abg_predict(fy);
+                            abg_predict(fz);
+                        }
+                        abg_update(fy, y);
+                        abg_update(fz, z);
+                    }
+                    rprev = row;
+                    if (k + 1 < len) {
+                        x = W.up[x];
+                        // the next hit is one row further, or two across a row the link skips
+                        if (row + 2 < nr && x >= __ldg(W.bin_off + rowbase + row + 2)) {
+                            slots[row + 1] = -1;
+                            row += 2;
+                        } else {
+                            row += 1;
+                        }
                     }
                 }
+                row_last = row;
             }
-            const int row_last = row;
             int r1, r0;
             const int n_out = extend(W, g, fy, fz, rowbase, row_last, +1, slots, &r1);
             // filter along the chain in descending rows from its last two hits
-            {
+            if constexpr (!SKIP) {
+                const int h1 = slots[row_last], h2 = slots[row_last - 1];
+                abg_init(fy, __ldg(W.pad + h1), __ldg(W.pad + h2), 1);
+                abg_init(fz, __ldg(W.tim + h1), __ldg(W.tim + h2), 1);
+                for (int k = len - 2; k >= 0; k--) {
+                    const int h = slots[row0 + k];
+                    abg_predict(fy);
+                    abg_predict(fz);
+                    abg_update(fy, __ldg(W.pad + h));
+                    abg_update(fz, __ldg(W.tim + h));
+                }
+            } else {
                 const int h1 = slots[row_last];
                 int rp = row_last;
                 bool first = true;
@@ -200,7 +237,10 @@ __global__ void __launch_bounds__(128) k_follow(Work W) {
 void launch_follow(const Work &W, cudaStream_t s) {
     const int block = W.tune.block[3] > 0 ? W.tune.block[3] : 128;
     const int grid = W.tune.grid[3] > 0 ? W.tune.grid[3] : W.sm_count * 8;
-    k_follow<<<grid, block, 0, s>>>(W);
+    if (W.rules & TPC_RULE_SKIP_ROW)
+        k_follow<true><<<grid, block, 0, s>>>(W);
+    else
+        k_follow<false><<<grid, block, 0, s>>>(W);
 }
 
 }  // namespace tpc

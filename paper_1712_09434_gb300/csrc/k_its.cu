@@ -30,8 +30,8 @@ constexpr double REF_MAX_SNP = 0.9;
 constexpr double TWO_PI = 6.283185307179586;
 
 // a - 2 pi n with n the nearest integer (IEEE remainder, exact): [-pi, pi]; no loop, so a corrupt
-// angle cannot stall the kernel
-__device__ __forceinline__ double wrap_pi(double a) { return remainder(a, TWO_PI); }
+// angle cannot stall the kernel.  |a| <= pi is its own remainder, so that case skips the call.
+__device__ __forceinline__ double wrap_pi(double a) { return fabs(a) <= 0.5 * TWO_PI ? a : remainder(a, TWO_PI); }
 
 __device__ __forceinline__ int phi_bin(double phi) {
     int b = (int)floor(phi / TWO_PI * ITS_NPHI);
@@ -47,12 +47,15 @@ struct ItsArgs {
     double kB, alpha0, dalpha; // curvature constant, sector k centre angle = alpha0 + (k mod half) dalpha
     int32_t *cnt, *off, *fill, *list, *sec;   // sec: 1 if the track may carry references
     unsigned long long *best_trk, *best_its;
+    double *sc;                // [n_its][2] sin, cos of phi0
 };
 
 __global__ void k_its_count(Work W, ItsArgs A) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_its; i += gridDim.x * blockDim.x) {
         const double phi = A.its[8 * (size_t)i];
         atomicAdd(A.cnt + phi_bin(phi), 1);
+        A.sc[2 * (size_t)i] = sin(phi);
+        A.sc[2 * (size_t)i + 1] = cos(phi);
         A.best_its[i] = ~0ull;
         A.match_its[i] = -1;
     }
@@ -126,6 +129,8 @@ __global__ void k_its_match(Work W, ItsArgs A) {
         A.sec[t] = first_row <= REF_MAX_FIRST_ROW && n_hits >= REF_MIN_HITS && fabs(s.p[2]) < REF_MAX_SNP;
         const double alpha = A.alpha0 + (k % g.half) * A.dalpha;
         const double phi_t = alpha + asin(s.p[2]);
+        const double sa = sin(alpha), ca = cos(alpha);
+        const float tl32 = (float)s.p[3], z32 = (float)s.p[1];
         const int ix[4] = {0, 2, 3, 4};
         unsigned long long best = ~0ull;
         const int b0 = (int)floor((phi_t - ITS_DPHI) / TWO_PI * ITS_NPHI), b1 = (int)floor((phi_t + ITS_DPHI) / TWO_PI * ITS_NPHI);
@@ -134,11 +139,15 @@ __global__ void k_its_match(Work W, ItsArgs A) {
             for (int j = A.off[b]; j < A.off[b + 1]; j++) {
                 const int i = A.list[j];
                 const float *r = A.its + 8 * (size_t)i;
+                // FP32 pre-checks with a margin that the exact tests below can only narrow
+                if (fabsf(r[2] - tl32) > (float)ITS_DTL + 1e-3f || fabsf(r[1] - z32) > (float)ITS_DZ + 1e-3f) continue;
                 if (fabs(wrap_pi((double)r[0] - phi_t)) > ITS_DPHI) continue;
                 if (fabs((double)r[2] - s.p[3]) > ITS_DTL || fabs((double)r[1] - s.p[1]) > ITS_DZ) continue;
-                const double dphi = wrap_pi((double)r[0] - alpha);
-                const double d[4] = {s.p[0], s.p[2] - sin(dphi), s.p[3] - (double)r[2], s.p[4] - (double)r[3]};
-                const double cph = cos(dphi) * (double)r[4];
+                // sin, cos of phi0 - alpha from those of phi0 and alpha (no transcendental per pair)
+                const double s0 = A.sc[2 * (size_t)i], c0 = A.sc[2 * (size_t)i + 1];
+                const double sdp = s0 * ca - c0 * sa, cdp = c0 * ca + s0 * sa;
+                const double d[4] = {s.p[0], s.p[2] - sdp, s.p[3] - (double)r[2], s.p[4] - (double)r[3]};
+                const double cph = cdp * (double)r[4];
                 const double ev[4] = {ITS_SIGMA_Y * ITS_SIGMA_Y, cph * cph, (double)r[6] * r[6], (double)r[7] * r[7]};
                 double M[4][4];
                 for (int a = 0; a < 4; a++)
@@ -206,6 +215,7 @@ void launch_its_match(const Work &W, const float *its, int n_its, int32_t *match
     A.sec = W.trk_n;
     A.best_trk = W.gap_bestT;
     A.best_its = W.gap_bestS;
+    A.sc = reinterpret_cast<double *>(W.gap_state);   // 6 words per chain slot >= 2 doubles per ITS track
     const int grid = W.sm_count * 4;
     cudaMemsetAsync(A.cnt, 0, sizeof(int32_t) * (ITS_NPHI + 1), s);
     cudaMemsetAsync(A.fill, 0, sizeof(int32_t) * (ITS_NPHI + 1), s);

@@ -241,8 +241,9 @@ __global__ void k_merge_match(Work W) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const float pitch = (float)(g.xtab[W.nr - 1] - g.xtab[0]) / (float)(W.nr - 1);
+    const bool gap = (W.rules & TPC_RULE_GAP_MERGE) != 0;
     for (int s = gw; s < n; s += nw) {
-        if (W.seg_n[s] < N_MIN || W.next[s] >= 0) continue;   // a gap successor: no outer end
+        if (W.seg_n[s] < N_MIN || (gap && W.next[s] >= 0)) continue;   // a gap successor: no outer end
         const int4 p1 = W.outend[2 * s], p2 = W.outend[2 * s + 1];
         const int ks = p1.w;
         const int ev = W.chain_bin[s] / (W.ns * W.nr);
@@ -281,7 +282,7 @@ __global__ void k_merge_match(Work W) {
             const int i1 = W.mrg_off[b0 + r_hi + 1];
             for (int i = W.mrg_off[b0 + r_lo] + lane; i < i1; i += 32) {
                 const int t = W.mrg_list[i];
-                if (W.prev[t] >= 0) continue;                        // a gap predecessor: no first segment
+                if (gap && W.prev[t] >= 0) continue;                 // a gap predecessor: no first segment
                 const int4 e = W.inend[t];
                 const long long XT = e.x;
                 const long long ax = XT - x2;
