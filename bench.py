@@ -34,12 +34,12 @@ sys.path.insert(0, ROOT)
 from paper_1712_09434_gb300 import synth  # noqa: E402
 
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
-# kernels of one step: tracking graph (bin offset check 2, grid 1, links 1, chains 8, follow 1,
-# select 1, merge 17, refit 1) + refit_grad (bin offset check 2, cluster bins 1, pack 1, length
-# sort 3, forward and reverse pass 2, reduce 2; the stored-state form adds the chunk lengths and
-# their scan, 4)
+# kernels of one step (one graph): tracking (bin offset check 2, grid 1, links 1, chains 8, follow 1,
+# select 1, merge 17, refit 1) + refit and adjoint of its tracks (length sort 3, forward and reverse
+# pass 2, reduce 2; the stored-state form adds the chunk lengths and their scan, 4; the hits were
+# packed and the bin offsets checked by the tracking part)
 LAUNCHES_TRACKING = 32
-LAUNCHES_REFIT_GRAD = {"checkpoints": 11, "stored states": 15}
+LAUNCHES_REFIT_GRAD = {"checkpoints": 7, "stored states": 11}
 
 
 def launches_per_step(tuning_best):

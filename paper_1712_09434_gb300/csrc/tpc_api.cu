@@ -230,17 +230,21 @@ struct RefitArgs {
 
 // Refit under theta and its adjoint for the tracks counted in *n_tracks_dev (S0, S8, S9), enqueued
 // on s.  With profiling on, events between the refit stages (external event nodes when capturing).
+// pack = false when the tracking part of the same stream order has just checked the bin offsets
+// and written the packed hits of exactly these tracks (the whole step as one graph).
 int enqueue_refit_grad(const tpc_ctx *c, const Work &W, const int32_t *n_tracks_dev, const double *theta,
                        const float *weight, const float *anchor, int model, double *sum_chi2, double *grad,
-                       cudaStream_t s, bool capturing) {
+                       cudaStream_t s, bool capturing, bool pack = true) {
     const bool prof = c->profile != 0;
     const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[0], s, evf));
     // the refit reads the track count from the workspace counters
     TPC_CUDA(cudaMemcpyAsync(W.counters + CNT_NTRACKS, n_tracks_dev, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
-    launch_bins_check(W, s);
-    launch_pack_hits(W, s);
+    if (pack) {
+        TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
+        launch_bins_check(W, s);
+        launch_pack_hits(W, s);
+    }
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[1], s, evf));
     launch_refit_grad_fit(W, theta, weight, anchor, model, grad != nullptr, c->ck, (long long)c->max_clusters + 1,
                           (long long)c->cap_chains + 1, c->rec, c->order, c->lhist, s);
@@ -276,7 +280,7 @@ int launch_graph(tpc_ctx *c, const Work &W, const RefitArgs *ra, cudaStream_t s)
         int erc = enqueue_pipeline(c, W, c->cap_stream, true);
         if (erc == TPC_OK && ra)
             erc = enqueue_refit_grad(c, W, W.n_tracks, ra->theta, ra->weight, ra->anchor, ra->model, ra->sum,
-                                     ra->grad, c->cap_stream, true);
+                                     ra->grad, c->cap_stream, true, false);
         const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
         if (erc != TPC_OK) {
             if (graph) cudaGraphDestroy(graph);
