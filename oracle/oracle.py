@@ -335,6 +335,40 @@ def its_match(fit_out, first_sector, its, g=None):
     return mt[:nt], mi[:ni], c2[:nt]
 
 
+def looper_pairs(fit_out, first_sector, event=None, g=None):
+    """Looper-leg pairing (see or_looper_pairs): fit_out = fit(...) of the tracks, first_sector =
+    sector of every track's first hit, event = event of every track (all 0 if None).  Returns
+    (partner of every track or -1, leg of every track: 1 outgoing, 2 returning, 0 unpaired,
+    D of each pair)."""
+    nt = int(fit_out["par"].shape[0])
+    ev = np.zeros(max(nt, 1), np.int32) if event is None else np.ascontiguousarray(event, np.int32)
+    pair = np.empty(max(nt, 1), np.int32)
+    leg = np.empty(max(nt, 1), np.int32)
+    D = np.zeros(max(nt, 1))
+    rc = lib().or_looper_pairs(_geom(g), ctypes.c_int32(nt), _p(np.ascontiguousarray(fit_out["par"], np.float64)),
+                               _p(np.ascontiguousarray(fit_out["xref"], np.float64)),
+                               _p(np.ascontiguousarray(fit_out["ndf"], np.int32)),
+                               _p(np.ascontiguousarray(first_sector, np.int32)), _p(ev), _p(pair), _p(leg), _p(D))
+    assert rc == 0, rc
+    return pair[:nt], leg[:nt], D[:nt]
+
+
+def loop_circle(par, xref, sector, ndf=1, g=None):
+    """(candidate?, centre x, centre y, R, far-point z, tan lambda, curvature sign) of one fitted
+    track (see or_loop_circle)."""
+    out = np.zeros(6)
+    ok = lib().or_loop_circle(_geom(g), _p(np.ascontiguousarray(par, np.float64)), ctypes.c_double(xref),
+                              ctypes.c_int32(sector), ctypes.c_int32(ndf), _p(out))
+    assert ok >= 0
+    return (bool(ok),) + tuple(out.tolist())
+
+
+def loop_constants():
+    buf = np.zeros(8)
+    k = lib().or_loop_constants(_p(buf), ctypes.c_int(8))
+    return dict(zip(["RMAX", "CMIN", "DC", "DR", "DZ", "DTL"], buf[:k].tolist()))
+
+
 def its_constants():
     buf = np.zeros(8)
     k = lib().or_its_constants(_p(buf), ctypes.c_int(8))

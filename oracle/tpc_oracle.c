@@ -17,7 +17,9 @@
  * (noise-free helices, chi2 statistics, least-squares optimum) and the gradient (central
  * differences of this file's own objective) are pinned by the CPU tests; the time-frame slice
  * merge by a constructed track cut by a slice boundary, the single-slice and whole-slice-delay
- * invariances and the truth of its links.  Track-finding efficiency on these synthetic events
+ * invariances and the truth of its links; the rules for inefficient data, the TPC-ITS matching
+ * and the looper-leg pairing by constructed cases at every window edge, exact tracks and the truth
+ * of their decisions on generated events.  Track-finding efficiency on these synthetic events
  * has no printed value in the paper: parity unpinned.
  */
 #define _USE_MATH_DEFINES
@@ -1300,3 +1302,117 @@ int or_its_constants(double *out, int cap) {
     return n;
 }
 
+
+/* ---- looper legs (reading of the segment merging of section 3 for low-pT loopers) ------------
+ * A particle with 2R inside the TPC goes out to the point of its circle farthest from the beam and
+ * comes back in: the tracker finds the two legs as two tracks, both fitted outwards in pad-row
+ * order, so the returning leg's fit has the opposite curvature and tan lambda of the outgoing one
+ * and the same circle.  Every fitted track with 1/|C| <= RMAX whose circle centre lies at least
+ * CMIN from the beam is a candidate: its circle (centre in the global frame, radius) and the z it
+ * reaches at the far point of the circle, carried along the fitted direction from its first hit
+ * (z + tan lambda * R * the turning angle to that point).  Two candidates of one event with
+ * opposite curvature are a pair when their centres are within DC, radii within DR, far-point z
+ * within DZ and |tan lambda_a + tan lambda_b| <= DTL; D = dcentre^2 + dR^2 + dz^2, and mutual
+ * best pairs by (floor(D 2^20), index) are joined.  The outgoing leg is the one whose |z| grows
+ * outwards (tan lambda times the side sign larger; the lower index on a tie). */
+#define OR_LOOP_RMAX  130.0
+#define OR_LOOP_CMIN  40.0
+#define OR_LOOP_DC    5.0
+#define OR_LOOP_DR    5.0
+#define OR_LOOP_DZ    8.0
+#define OR_LOOP_DTL   0.05
+
+typedef struct { double cx, cy, R, zap, tl, sgn; int ok, side; } or_loop;
+
+static or_loop loop_circle(const or_geom *g, const double *p, double xref, int sector, int ndf) {
+    or_loop L;
+    memset(&L, 0, sizeof(L));
+    if (ndf <= 0 || !(fabs(p[2]) < 1.0)) return L;
+    const double C = g->kB * p[4];
+    if (!(fabs(C) * OR_LOOP_RMAX >= 1.0)) return L;
+    const double sp = p[2], cp = sqrt(1.0 - sp * sp);
+    /* centre of curvature in the sector frame: the point 1/C to the left of the direction */
+    const double lx = xref - sp / C, ly = p[0] + cp / C;
+    const double alpha = ((sector % (g->n_sectors / 2)) + 0.5) * 2.0 * g->half_angle;
+    const double ca = cos(alpha), sa = sin(alpha);
+    L.cx = lx * ca - ly * sa;
+    L.cy = lx * sa + ly * ca;
+    const double rc = sqrt(L.cx * L.cx + L.cy * L.cy);
+    if (!(rc >= OR_LOOP_CMIN)) return L;
+    L.R = 1.0 / fabs(C);
+    /* first hit and far point of the circle, global frame */
+    const double hx = xref * ca - p[0] * sa, hy = xref * sa + p[0] * ca;
+    const double fx = L.cx + L.R * L.cx / rc, fy = L.cy + L.R * L.cy / rc;
+    const double a_h = atan2(hy - L.cy, hx - L.cx), a_f = atan2(fy - L.cy, fx - L.cx);
+    double turn = (a_f - a_h) * (C > 0.0 ? 1.0 : -1.0);   /* turning angle along the fit direction */
+    turn = fmod(turn, 2.0 * OR_PI);
+    if (turn < 0.0) turn += 2.0 * OR_PI;
+    L.zap = p[1] + p[3] * L.R * turn;
+    L.tl = p[3];
+    L.sgn = C > 0.0 ? 1.0 : -1.0;
+    L.side = sector < g->n_sectors / 2 ? 1 : -1;
+    L.ok = 1;
+    return L;
+}
+
+int or_looper_pairs(const or_geom_in *gin, int32_t n_trk, const double *par, const double *xref,
+                    const int32_t *ndf, const int32_t *sector, const int32_t *event, int32_t *pair, int32_t *leg,
+                    double *D_out) {
+    or_geom g;
+    if (make_geom(gin, &g)) return -1;
+    or_loop *L = (or_loop *)malloc(sizeof(or_loop) * (n_trk + 1));
+    int64_t *best = (int64_t *)malloc(sizeof(int64_t) * (n_trk + 1));
+    double *bD = (double *)malloc(sizeof(double) * (n_trk + 1));
+    const int64_t SHIFT = (int64_t)1 << 32;
+    for (int32_t t = 0; t < n_trk; t++) {
+        L[t] = loop_circle(&g, par + 5 * (int64_t)t, xref[t], sector[t], ndf[t]);
+        best[t] = -1;
+        bD[t] = 0.0;
+        pair[t] = -1;
+        if (leg) leg[t] = 0;
+    }
+    for (int32_t a = 0; a < n_trk; a++) {
+        if (!L[a].ok) continue;
+        for (int32_t b = 0; b < n_trk; b++) {
+            if (b == a || !L[b].ok || event[b] != event[a] || L[b].sgn == L[a].sgn) continue;
+            const double dx = L[a].cx - L[b].cx, dy = L[a].cy - L[b].cy;
+            const double dc2 = dx * dx + dy * dy, dR = L[a].R - L[b].R, dz = L[a].zap - L[b].zap;
+            if (dc2 > OR_LOOP_DC * OR_LOOP_DC || fabs(dR) > OR_LOOP_DR || fabs(dz) > OR_LOOP_DZ) continue;
+            if (fabs(L[a].tl + L[b].tl) > OR_LOOP_DTL) continue;
+            const double D = dc2 + dR * dR + dz * dz;
+            const int64_t k = (int64_t)floor(D * 1048576.0) * SHIFT + b;
+            if (best[a] < 0 || k < best[a]) { best[a] = k; bD[a] = D; }
+        }
+    }
+    for (int32_t a = 0; a < n_trk; a++) {
+        if (best[a] < 0) continue;
+        const int32_t b = (int32_t)(best[a] % SHIFT);
+        if (best[b] < 0 || (int32_t)(best[b] % SHIFT) != a) continue;
+        pair[a] = b;
+        if (D_out) D_out[a] = bD[a];
+        if (leg) {
+            const double ua = L[a].tl * L[a].side, ub = L[b].tl * L[b].side;
+            leg[a] = (ua > ub || (ua == ub && a < b)) ? 1 : 2;
+        }
+    }
+    free(L); free(best); free(bD);
+    return 0;
+}
+
+int or_loop_constants(double *out, int cap) {
+    const double v[] = {OR_LOOP_RMAX, OR_LOOP_CMIN, OR_LOOP_DC, OR_LOOP_DR, OR_LOOP_DZ, OR_LOOP_DTL};
+    int n = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < n && i < cap; i++) out[i] = v[i];
+    return n;
+}
+
+/* The candidate description of one fitted track (test access): out = centre x, y (global), R,
+ * far-point z, tan lambda, curvature sign; returns 1 for a candidate, 0 otherwise. */
+int or_loop_circle(const or_geom_in *gin, const double *par, double xref, int32_t sector, int32_t ndf,
+                   double *out) {
+    or_geom g;
+    if (make_geom(gin, &g)) return -1;
+    const or_loop L = loop_circle(&g, par, xref, sector, ndf);
+    out[0] = L.cx; out[1] = L.cy; out[2] = L.R; out[3] = L.zap; out[4] = L.tl; out[5] = L.sgn;
+    return L.ok;
+}
