@@ -576,6 +576,25 @@ def run_native(args, rank, world):
     match_out = {"ms_per_event": ms_match, "tracks": nt5, "its_tracks": int(its5.shape[0]),
                  "matched": int(mm.sum()), "right_particle": float((its_part[mt5[mm]] == lead5[mm]).mean()),
                  "to_fakes": int((its_part[mt5[mm]] < 0).sum()), "with_references": int((ref5[:, 0] > 0).sum())}
+    # looper legs of the same event: pairs, their truth, and the loopers whose two legs were found
+    pair5 = torch.empty(nt5, dtype=torch.int32, device=dev)
+    leg5 = torch.empty(nt5, dtype=torch.int32, device=dev)
+    ms_loop, _ = timed(lambda: ctx.tpc_looper_pairs(c5, t5, pair5, leg5), 10, 3)
+    p5 = pair5.cpu().numpy()
+    pm = p5 >= 0
+    kB = abs(synth.KB)
+    s_med = np.array([np.nanmedian(ev5.true_s[h5["trk_hits"][a:b]]) if b > a else np.nan
+                      for a, b in zip(h5["trk_off"][:-1], h5["trk_off"][1:])])
+    half = np.pi * ev5.trk_pt[lead5] / kB            # path length of the far point of each track's particle
+    loops = (2 * ev5.trk_pt / kB < synth.R_OUT)      # particles whose circle stays inside the TPC
+    out_leg = loops[lead5] & (s_med < half)
+    ret_leg = loops[lead5] & (s_med >= half)
+    both = np.intersect1d(lead5[out_leg], lead5[ret_leg])
+    joined = np.unique(lead5[pm & (lead5 == lead5[np.maximum(p5, 0)])])
+    loop_out = {"ms_per_event": ms_loop, "pairs": int(pm.sum() // 2),
+                "same_particle": float((lead5[pm] == lead5[p5[pm]]).mean()) if pm.any() else None,
+                "loopers_with_both_legs_found": int(both.size),
+                "of_them_joined": float(np.isin(both, joined).mean()) if both.size else None}
     th5 = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
     # the adjoint as specified: per-row Kalman states recomputed in the reverse sweep from checkpoints
     # (every 16 steps); then the variant that stores every step's input state (100 B per hit)
@@ -632,7 +651,7 @@ def run_native(args, rank, world):
                  "sum_chi2_start_end": [cres.history[0][1], cres.history[-1][1]],
                  "tracks_with_reference": int((ref5[:, 0] > 0).sum())}
 
-    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, ms_grad_event_stored=ms_grad_stored, its_match=match_out,
+    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, ms_grad_event_stored=ms_grad_stored, its_match=match_out, loopers=loop_out,
                inefficient=rules_out,
                n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
                weighted_hits=weighted_hits,
@@ -738,6 +757,7 @@ def finish_native(args, res, world):
                                               "identical gradient"}},
         "calibration": res["calib"],
         "its_match": res.get("its_match"),
+        "looper_legs": res.get("loopers"),
         "inefficient_data": res.get("inefficient"),
         "single_event": res["single"],
         "time_frame": res["frame"],

@@ -199,6 +199,28 @@ int tpc_track_refit_batch(tpc_ctx *ctx, const tpc_clusters *in, tpc_tracks *out,
 int tpc_its_match(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, const float *its, int32_t n_its,
                   int32_t *match_trk, int32_t *match_its, float *anchor, void *stream);
 
+/* Looper-leg pairing (section 3 of the paper merges the track segments that the sector tracking
+ * finds; this joins the two legs of a low-pT looper, which leave the tracking as two tracks).
+ *  - in: the clusters the tracks were found on; trk: tracks with their fit (trk_off, trk_hits, par,
+ *    xref, ndf, n_tracks as a tracking call writes them).  Tracks beyond the context's chain
+ *    capacity (clusters / 5) are not considered (TPC_ERR_CAPACITY via tpc_sync_status).
+ *  - Rule: both legs are fitted outwards in pad-row order, so the returning leg has the opposite
+ *    curvature and tan lambda of the outgoing one on the same circle.  From every fitted state (at
+ *    the first hit, in that hit's sector frame; FP64): the centre of curvature in the global frame,
+ *    the radius R = 1/|C| and the z reached at the point of the circle farthest from the beam, along
+ *    the fitted direction.  Candidates have R <= 130 cm and a centre >= 40 cm from the beam.  Two
+ *    candidates of one event with opposite curvature pair if their centres are within 5 cm, radii
+ *    within 5 cm, far-point z within 8 cm and |tan lambda_a + tan lambda_b| <= 0.05; mutual best
+ *    pairs by (floor(D * 2^20), index), D = dcentre^2 + dR^2 + dz^2 (cm^2), are joined.
+ *  - Outputs (device, [n_tracks]): pair[t] = the other leg or -1; if leg is not NULL, leg[t] = 1 for
+ *    the outgoing leg (the one whose |z| grows outwards; the lower index if both tan lambda are
+ *    equal), 2 for the returning leg, 0 for an unpaired track.  The joined looper is the outgoing
+ *    leg's hits followed by the returning leg's in reverse order; each leg keeps its own fit.
+ * Errors: INVALID_ARG, NOT_RESERVED, CAPACITY, CUDA; BOUNDS (a hit outside the clusters) via
+ * tpc_sync_status. */
+int tpc_looper_pairs(tpc_ctx *ctx, const tpc_clusters *in, const tpc_tracks *trk, int32_t *pair, int32_t *leg,
+                     void *stream);
+
 /* Time-frame slice merge (arxiv 1712.09434 section 3, its outlook for continuous readout: a time
  * frame of many overlapping collisions is cut along the drift-time axis, the slices are tracked
  * one by one, and the track segments are merged afterwards).
@@ -256,6 +278,13 @@ int tpc_set_rules(tpc_ctx *ctx, int32_t rules);
 /* The rule bits and GAP_MAX, for comparison with an independent implementation.  Returns the count
  * written (at most cap). */
 int tpc_rule_constants(int64_t *out, int32_t cap);
+
+/* The reading constants of the matching steps, for comparison with an independent implementation:
+ * TPC-ITS matching (sigma_y of an ITS track at the vertex, azimuth window, tan lambda window, z window,
+ * chi2 gate), then looper-leg pairing (largest radius, smallest centre distance from the beam,
+ * centre, radius and far-point z gates in cm, tan lambda sum gate).  Writes min(n, cap) values to out
+ * (host) and returns n = 11. */
+int tpc_match_constants(double *out, int32_t cap);
 
 /* Wait for `stream` and return the device status word of the last calls (then clear it). */
 int tpc_sync_status(tpc_ctx *ctx, void *stream);

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpc.so")
 SOURCES = ["tpc_api.cu", "k_scan.cu", "k_links.cu", "k_chains.cu", "k_follow.cu", "k_select.cu", "k_merge.cu", "k_frame.cu",
-           "k_refit.cu", "k_peak.cu", "k_its.cu"]
+           "k_refit.cu", "k_peak.cu", "k_its.cu", "k_loop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -88,6 +88,7 @@ def _load():
     lib.tpc_rule_constants.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
     lib.tpc_its_match.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, i32, vp, vp, vp,
                                   vp]
+    lib.tpc_looper_pairs.argtypes = [vp, ctypes.POINTER(tpc_clusters), ctypes.POINTER(tpc_tracks), vp, vp, vp]
     lib.tpc_set_rules.argtypes = [vp, i32]
     lib.tpc_links_noalloc.argtypes = [ctypes.POINTER(tpc_geometry), ctypes.POINTER(tpc_clusters), vp, vp, vp, vp]
     lib.tpc_selftest_wait_timeout.argtypes = [vp, i32, vp]
@@ -273,6 +274,13 @@ class Context:
         n_its = int(its.shape[0]) if its is not None else 0
         check(_lib.tpc_its_match(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(its), n_its, _ptr(match_trk),
                                  _ptr(match_its), _ptr(anchor), _stream(stream)), "tpc_its_match")
+
+    def tpc_looper_pairs(self, clusters, tracks, pair, leg=None, stream=None):
+        """Pair the two legs of every looper among the fitted tracks (device int32 [n_tracks] outputs);
+        see include/tpc.h."""
+        cs, ts = clusters.struct(), tracks.struct()
+        check(_lib.tpc_looper_pairs(self.handle, ctypes.byref(cs), ctypes.byref(ts), _ptr(pair), _ptr(leg),
+                                    _stream(stream)), "tpc_looper_pairs")
 
     def tpc_merge_slices(self, clusters, slice_tracks, slice_len, frame, stream=None):
         """Join the tracks of consecutive time slices into frame tracks (see tpc_merge_slices)."""

@@ -194,6 +194,11 @@ __global__ void k_its_link(Work W, ItsArgs A) {
 }  // namespace
 
 int its_match_nphi() { return ITS_NPHI; }
+int its_constants(double *out) {
+    const double v[] = {ITS_SIGMA_Y, ITS_DPHI, ITS_DTL, ITS_DZ, ITS_CHI2};
+    for (int i = 0; i < 5; i++) out[i] = v[i];
+    return 5;
+}
 
 void launch_its_match(const Work &W, const float *its, int n_its, int32_t *match_trk, int32_t *match_its,
                       float *anchor, double kB, double alpha0, double dalpha, cudaStream_t s) {

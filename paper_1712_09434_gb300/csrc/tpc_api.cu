@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/tpc.h: context, workspace, argument validation,
 // the per-event pipeline, its CUDA-graph replay for batches, and the refit/adjoint call.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -512,6 +513,27 @@ int tpc_its_match(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, con
     return cuda_err(cudaGetLastError());
 }
 
+int tpc_looper_pairs(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, int32_t *pair, int32_t *leg,
+                     void *stream) {
+    if (!c || !trk || !trk->trk_off || !trk->trk_hits || !trk->par || !trk->xref || !trk->ndf || !trk->n_tracks ||
+        trk->cap_tracks < 1 || !pair)
+        return TPC_ERR_INVALID_ARG;
+    int rc = validate_in(c, in);
+    if (rc) return rc;
+    if ((long long)in->n_events * loop_nphi() > c->nbins_max) return TPC_ERR_CAPACITY;
+    const Work W = make_work(c, in, trk, nullptr);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
+    launch_bins_check(W, s);
+    // candidate records (8 doubles per track) in the refit workspace, which is free between calls
+    const long long rec_tracks = (long long)refit_ck_words((long long)c->max_clusters + 1, (long long)c->cap_chains + 1) / 16;
+    const int nt_cap = (int)std::min<long long>(c->cap_chains, rec_tracks);
+    const double ha = c->geom.half_angle_deg * M_PI / 180.0;
+    launch_looper_pairs(W, pair, leg, -0.299792458e-2 * c->bz, ha, 2.0 * ha, reinterpret_cast<double *>(c->ck),
+                        nt_cap, s);
+    return cuda_err(cudaGetLastError());
+}
+
 int tpc_merge_slices(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *slice_trk, int32_t slice_len,
                      tpc_tracks *frame, void *stream) {
     if (!c) return TPC_ERR_INVALID_ARG;
@@ -581,6 +603,15 @@ int tpc_set_rules(tpc_ctx *c, int32_t rules) {
     if (!c || (rules & ~(TPC_RULE_SKIP_ROW | TPC_RULE_GAP_MERGE))) return TPC_ERR_INVALID_ARG;
     c->rules = rules;
     return TPC_OK;
+}
+
+int tpc_match_constants(double *out, int32_t cap) {
+    double v[16];
+    int n = its_constants(v);
+    n += loop_constants(v + n);
+    if (out)
+        for (int i = 0; i < n && i < cap; i++) out[i] = v[i];
+    return n;
 }
 
 int tpc_rule_constants(int64_t *out, int32_t cap) {

@@ -207,6 +207,11 @@ void launch_pack_hits(const Work &W, cudaStream_t s);
 void launch_its_match(const Work &W, const float *its, int n_its, int32_t *match_trk, int32_t *match_its,
                       float *anchor, double kB, double alpha0, double dalpha, cudaStream_t s);
 int its_match_nphi();
+void launch_looper_pairs(const Work &W, int32_t *pair, int32_t *leg, double kB, double alpha0, double dalpha,
+                         double *rec, int nt_cap, cudaStream_t s);
+int loop_nphi();
+int its_constants(double *out);     // 5 values
+int loop_constants(double *out);    // 6 values
 void prepare_kernels();
 // device-wide exclusive scan of n (host) or *n_dev (device, if not NULL) int32 values; writes
 // out[0..n] (out[n] = total) and *total_dev (if not NULL).

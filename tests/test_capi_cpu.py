@@ -46,6 +46,14 @@ def test_rule_constants_match_oracle(lib_path):
     assert [buf[i] for i in range(n)] == list(O.rule_constants().values())
 
 
+def test_match_constants_match_oracle(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    buf = (ctypes.c_double * 16)()
+    n = lib.tpc_match_constants(buf, 16)
+    assert n == 11
+    assert [buf[i] for i in range(n)] == list(O.its_constants().values()) + list(O.loop_constants().values())
+
+
 def test_strerror_covers_codes(lib_path):
     lib = ctypes.CDLL(lib_path)
     lib.tpc_strerror.restype = ctypes.c_char_p
