@@ -891,6 +891,47 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------------------------------
 
+def adjoint_event(form, calls=10):
+    """Refit + adjoint of the central calibration event (references from the TPC-ITS matching, raw
+    errors) in one form, library default launch shapes otherwise: ms per call."""
+    import numpy as np
+    import torch
+    from paper_1712_09434_gb300 import capi, tune
+    dev = "cuda"
+    ev = synth.make_event(synth.calib_event())
+    cl = capi.Clusters.from_numpy(ev.pad_fp, ev.time_fp, ev.bin_off, 1)
+    tr = capi.Tracks(ev.n_clusters, 1, ev.n_clusters // 8 + 1024, ev.n_clusters)
+    ctx = capi.Context(max_clusters=ev.n_clusters, max_events=1)
+    ctx.tpc_track_event(cl, tr)
+    h = tr.to_host()
+    nt = h["n_tracks"]
+    w = torch.tensor(((h["ndf"] > 0) & (h["chi2"] < 5.0 * np.maximum(h["ndf"], 1))).astype(np.float32), device=dev)
+    its, _ = synth.its_tracks(ev)
+    its_d = torch.tensor(its.astype(np.float32), device=dev)
+    m_trk = torch.empty(nt, dtype=torch.int32, device=dev)
+    m_its = torch.empty(its.shape[0], dtype=torch.int32, device=dev)
+    anchor = torch.zeros((nt, 8), dtype=torch.float32, device=dev)
+    ctx.tpc_its_match(cl, tr, its_d, m_trk, m_its, anchor)
+    th = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
+    s_chi2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.zeros(1 + 2 * synth.N_SECTORS, dtype=torch.float64, device=dev)
+    ctx.tpc_set_tuning(tune.to_struct({"refit_grad": (0, 0, 1)}) if form == "stored" else None)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(calls):
+        e0.record(stream)
+        ctx.tpc_refit_grad(cl, tr, th, s_chi2, grad, w, anchor, 1)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    st = ctx.tpc_sync_status()
+    ctx.close()
+    assert st == 0, st
+    return {"adjoint_form": form, "tracks": nt, "ms_per_call": float(np.median(ts)), "calls": calls,
+            "note": "--only-adjoint (profiling run)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -904,6 +945,9 @@ def main():
     ap.add_argument("--store-tuning", default=None, help="write the autotuned shapes to this JSON cache")
     ap.add_argument("--only-step", action="store_true",
                     help="time the batched step only (no plain/adjoint/e2e/CPU legs); for profiling")
+    ap.add_argument("--only-adjoint", default=None, choices=["checkpoints", "stored"],
+                    help="time the refit + adjoint of the central calibration event only, in one form; "
+                         "for profiling")
     ap.add_argument("--fp32-peak", action="store_true",
                     help="measure the FP32 FMA throughput of the GPU only (the roof of the Kalman stages)")
     args = ap.parse_args()
@@ -913,6 +957,11 @@ def main():
         __graft_entry__.build()
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps({"fp32_peak": fp32_peak(seconds=2.0)}), flush=True)
+        return
+    if args.only_adjoint:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(adjoint_event(args.only_adjoint)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
