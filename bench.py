@@ -399,20 +399,21 @@ def run_native(args, rank, world):
     ref_red = torch.cat([s_chi2, grad]).cpu()
 
     # pipelined: the two contexts of the timed steps take the steps in turn, each on its own compute
-    # stream.  Every context has two input buffer sets, so that a step's inputs are copied in while
-    # the context's previous step still computes, and its results are copied to a device staging
-    # set right after its compute (a fast device copy), from which they go to the host on a copy
-    # stream while the next steps compute: no context waits for a host transfer.
+    # stream.  Every context has two buffer sets, inputs and outputs, used by its steps in turn: a
+    # step's inputs are copied in while the context's previous step (on the other set) computes, and
+    # its results go to the host on a copy stream straight from the output buffers while the next
+    # steps compute; a set is reused only after its results reached the host.  No context waits for a
+    # host transfer, and no device copy of the results is made.
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
     def dev_inputs():
         return capi.Clusters(torch.empty_like(d_pad), torch.empty_like(d_tim), torch.empty_like(d_bo), n_ev)
 
     cls = [[cl, dev_inputs()], [cl2, dev_inputs()]]
-    trs = [tr, tr2]
-    reds = [(s_chi2, grad), (s_chi2_2, grad_2)]
-    stage = [[tuple(torch.empty_like(x) for x in out_views(tr)) + (torch.empty(74, dtype=torch.float64, device=dev),)
-              for _ in range(2)] for _ in range(2)]
+    trs = [[tr, capi.Tracks(n_clusters, n_ev, cap_t, n_clusters)],
+           [tr2, capi.Tracks(n_clusters, n_ev, cap_t, n_clusters)]]
+    reds = [[(s_chi2, grad), (torch.empty_like(s_chi2), torch.empty_like(grad))],
+            [(s_chi2_2, grad_2), (torch.empty_like(s_chi2), torch.empty_like(grad))]]
     h_outs = [[h_seq, host_set()], [host_set(), host_set()]]
     ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
     ev_comp = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
@@ -421,8 +422,8 @@ def run_native(args, rank, world):
     def e2e_pipelined(n_steps, first=0):
         for k in range(first, first + n_steps):
             b, j = k % 2, (k // 2) % 2                    # context, buffer set of this context
-            c, t_, (sc, gr) = cls[b][j], trs[b], reds[b]
-            st, ho = stage[b][j], h_outs[b][j]
+            c, t_, (sc, gr) = cls[b][j], trs[b][j], reds[b][j]
+            ho = h_outs[b][j]
             cx, cs = lanes[b][0], lanes[b][5]
             with torch.cuda.stream(s_in):                 # inputs (free once this set's last step ran)
                 s_in.wait_event(ev_comp[b][j])
@@ -431,18 +432,15 @@ def run_native(args, rank, world):
                 c.bin_off.copy_(h_bo, non_blocking=True)
                 ev_in[b][j].record(s_in)
             cs.wait_event(ev_in[b][j])
+            cs.wait_event(ev_out[b][j])                   # this set's last results are on the host
             cx.tpc_track_refit_batch(c, t_, theta, sc, gr, w_batch, stream=cs)
-            cs.wait_event(ev_out[b][j])                   # this staging set is on the host already
-            with torch.cuda.stream(cs):                   # results to device staging
-                for dst, src in zip(st[:-1], out_views(t_)):
-                    dst.copy_(src, non_blocking=True)
-                st[-1][:1].copy_(sc, non_blocking=True)
-                st[-1][1:].copy_(gr, non_blocking=True)
             ev_comp[b][j].record(cs)
-            with torch.cuda.stream(s_out):                # staging to the host
+            with torch.cuda.stream(s_out):                # results to the host
                 s_out.wait_event(ev_comp[b][j])
-                for dst, src in zip(ho, st):
+                for dst, src in zip(ho[:-1], out_views(t_)):
                     dst.copy_(src, non_blocking=True)
+                ho[-1][:1].copy_(sc, non_blocking=True)
+                ho[-1][1:].copy_(gr, non_blocking=True)
                 ev_out[b][j].record(s_out)
         stream.wait_stream(s_in)
         for lane_ in lanes:
@@ -469,8 +467,8 @@ def run_native(args, rank, world):
     assert ctx.tpc_sync_status() == 0 and ctx2.tpc_sync_status() == 0
     ms_e2e, _ = aggregate(ms_e2e, n_clusters, world, dev)
     # every host result set (both contexts, both buffer sets: the last steps of the timed loop) must
-    # equal the device-resident result bit for bit; a race between a staging copy and the next
-    # step's outputs would show here
+    # equal the device-resident result bit for bit; a race between a host copy and the next step
+    # writing the same output set would show here
     torch.cuda.synchronize()
     nt, nh = res["n_tracks"], int(res["trk_off"][-1])
     want = (res["label"][:n_clusters], res["trk_off"], res["trk_hits"], res["ev_trk_off"][:n_ev + 1],
@@ -775,7 +773,7 @@ def finish_native(args, res, world):
         "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": res["h2d"],
                 "d2h_bytes_per_step": res["d2h"],
                 "form": "through the binding from pinned host buffers; two contexts taking the steps in turn, "
-                        "two input sets per context, results staged on the device; host copies on their "
+                        "two input and output buffer sets per context used in turn; host copies on their "
                         "own streams overlapping the compute; every step copies the whole result set back "
                         "(labels, track offsets and hits, event offsets, parameters, reference x, "
                         "covariances, chi2, ndf, track count, sum of chi2 and gradient)",
