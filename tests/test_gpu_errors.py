@@ -172,4 +172,17 @@ def test_malformed_bin_offsets_are_a_bounds_error_with_nothing_written_outside(k
     th = torch.tensor(synth.theta_nominal(), dtype=torch.float64, device="cuda")
     ctx.tpc_refit_grad(bad, good["tracks_obj"], th, s, None)
     assert ctx.tpc_sync_status() == capi.TPC_ERR_BOUNDS
+    # the matching steps that look up the first hit's sector in the offsets: bounds errors too, and
+    # nothing written past their outputs
+    nt = good["n_tracks"]
+    pair = torch.full((nt + tail,), 777, dtype=torch.int32, device="cuda")
+    ctx.tpc_looper_pairs(bad, good["tracks_obj"], pair[:nt])
+    assert ctx.tpc_sync_status() == capi.TPC_ERR_BOUNDS
+    assert bool((pair[nt:] == 777).all())
+    its = torch.zeros((4, 8), dtype=torch.float32, device="cuda")
+    mt = torch.full((nt + tail,), 777, dtype=torch.int32, device="cuda")
+    mi = torch.full((4 + tail,), 777, dtype=torch.int32, device="cuda")
+    ctx.tpc_its_match(bad, good["tracks_obj"], its, mt[:nt], mi[:4])
+    assert ctx.tpc_sync_status() == capi.TPC_ERR_BOUNDS
+    assert bool((mt[nt:] == 777).all()) and bool((mi[4:] == 777).all())
     ctx.close()
