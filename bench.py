@@ -41,7 +41,6 @@ METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-gra
 LAUNCHES_TRACKING = 32
 LAUNCHES_REFIT_GRAD = {"checkpoints": 7, "stored states": 11}
 
-
 def launches_per_step(tuning_best):
     form = "stored states" if tuning_best and tuple(tuning_best.get("refit_grad", (0, 0, 0)))[2] == 1 else "checkpoints"
     return LAUNCHES_TRACKING + LAUNCHES_REFIT_GRAD[form], form
@@ -227,7 +226,13 @@ def run_native(args, rank, world):
     n_clusters = int(d["pad"].shape[0])
     n_ev = args.events
     cl = capi.Clusters.from_numpy(d["pad"], d["tim"], d["bin_off"], n_ev)
-    cap_t = n_clusters // 10 + 1024        # a track has at least 10 hits
+    # track capacity of the outputs: one track per 64 clusters, 2.4 times the 218,673 tracks of the
+    # 64-event batch and 1.9 times the 272,526 slice tracks of its time frame (beyond it the library
+    # reports CAPACITY, which every timed leg checks).  It sizes the per-track result arrays that the
+    # end-to-end leg copies back every step; at one track per 10 clusters (the bound from the 10-hit
+    # minimum) they are 585 instead of 316 MB, and the larger host transfers slow the overlapped
+    # compute (measured 2.5 against 2.9e9 clusters/s end to end)
+    cap_t = n_clusters // 64 + 1024
     ctx = capi.Context(max_clusters=n_clusters, max_events=n_ev)
     tr = capi.Tracks(n_clusters, n_ev, cap_t, n_clusters)
     theta = torch.tensor(synth.theta_nominal(), dtype=torch.float64, device=dev)
@@ -404,7 +409,11 @@ def run_native(args, rank, world):
     # its results go to the host on a copy stream straight from the output buffers while the next
     # steps compute; a set is reused only after its results reached the host.  No context waits for a
     # host transfer, and no device copy of the results is made.
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    # one input and one result copy stream per context, so that one context's copies never queue
+    # behind the other's
+    s_ins = [torch.cuda.Stream(), torch.cuda.Stream()]
+    s_outs = [torch.cuda.Stream(), torch.cuda.Stream()]
+    s_out = s_outs[0]
 
     def dev_inputs():
         return capi.Clusters(torch.empty_like(d_pad), torch.empty_like(d_tim), torch.empty_like(d_bo), n_ev)
@@ -425,6 +434,7 @@ def run_native(args, rank, world):
             c, t_, (sc, gr) = cls[b][j], trs[b][j], reds[b][j]
             ho = h_outs[b][j]
             cx, cs = lanes[b][0], lanes[b][5]
+            s_in, s_out = s_ins[b], s_outs[b]
             with torch.cuda.stream(s_in):                 # inputs (free once this set's last step ran)
                 s_in.wait_event(ev_comp[b][j])
                 c.pad_fp.copy_(h_pad, non_blocking=True)
@@ -442,28 +452,30 @@ def run_native(args, rank, world):
                 ho[-1][:1].copy_(sc, non_blocking=True)
                 ho[-1][1:].copy_(gr, non_blocking=True)
                 ev_out[b][j].record(s_out)
-        stream.wait_stream(s_in)
+        for s_ in s_ins + s_outs:
+            stream.wait_stream(s_)
         for lane_ in lanes:
             stream.wait_stream(lane_[5])
-        stream.wait_stream(s_out)
 
     n_pipe = max(8, min(args.steps, 40))
     e2e_pipelined(4)                       # warm: every buffer set of both contexts captured once
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    flush.fill_(1.0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for lane_ in lanes:
-        lane_[5].wait_event(e0)
-    s_in.wait_event(e0)
-    s_out.wait_event(e0)
-    e2e_pipelined(n_pipe, first=4)
-    e1.record(stream)
-    e1.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / n_pipe
+    # three timed windows of n_pipe steps each; the line reports their median and lists all three
+    ms_windows = []
+    for w_ in range(3):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s_ in [lane_[5] for lane_ in lanes] + s_ins + s_outs:
+            s_.wait_event(e0)
+        e2e_pipelined(n_pipe, first=4 + 4 * n_pipe * w_)
+        e1.record(stream)
+        e1.synchronize()
+        ms_windows.append(e0.elapsed_time(e1) / n_pipe)
+    ms_e2e = float(np.median(ms_windows))
     assert ctx.tpc_sync_status() == 0 and ctx2.tpc_sync_status() == 0
     ms_e2e, _ = aggregate(ms_e2e, n_clusters, world, dev)
     # every host result set (both contexts, both buffer sets: the last steps of the timed loop) must
@@ -487,7 +499,36 @@ def run_native(args, rank, world):
                 raise RuntimeError("end-to-end sum of chi2 / gradient of context %d, set %d differs" % (b, j))
             e2e_checked += 1
 
-    out.update(ms_e2e=ms_e2e, ms_e2e_seq=ms_e2e_seq, h2d=h2d, d2h=d2h, e2e_checked=e2e_checked)
+    # the host link alone: one step's input copies, and one step's result copies, with no compute
+    def copies(direction):
+        with torch.cuda.stream(s_out):
+            for _ in range(5):
+                if direction == "h2d":
+                    d_pad.copy_(h_pad, non_blocking=True)
+                    d_tim.copy_(h_tim, non_blocking=True)
+                    d_bo.copy_(h_bo, non_blocking=True)
+                else:
+                    for dst, src in zip(h_outs[1][1][:-1], out_views(tr)):
+                        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(s_out)
+        with torch.cuda.stream(s_out):
+            for _ in range(10):
+                if direction == "h2d":
+                    d_pad.copy_(h_pad, non_blocking=True)
+                    d_tim.copy_(h_tim, non_blocking=True)
+                    d_bo.copy_(h_bo, non_blocking=True)
+                else:
+                    for dst, src in zip(h_outs[1][1][:-1], out_views(tr)):
+                        dst.copy_(src, non_blocking=True)
+        c1.record(s_out)
+        c1.synchronize()
+        return c0.elapsed_time(c1) / 10
+
+    link_ms = {"h2d_ms_per_step": copies("h2d"), "d2h_ms_per_step": copies("d2h")}
+    out.update(ms_e2e=ms_e2e, ms_e2e_seq=ms_e2e_seq, h2d=h2d, d2h=d2h, e2e_checked=e2e_checked, link_ms=link_ms,
+               e2e_windows=[n_cl_all / (m * 1e-3) for m in ms_windows])
     if rank != 0:
         return out
 
@@ -779,7 +820,9 @@ def finish_native(args, res, world):
                         "covariances, chi2, ndf, track count, sum of chi2 and gradient)",
                 "checked": "%d host result sets equal to the device-resident result bit for bit" %
                            res.get("e2e_checked", 0),
-                "sequential_value": n_cl_total / (res["ms_e2e_seq"] * 1e-3)},
+                "sequential_value": n_cl_total / (res["ms_e2e_seq"] * 1e-3),
+                "host_link_alone": res.get("link_ms"),
+                "windows": res.get("e2e_windows")},
         "gpu_launches": n_launch * args.steps,
         "clocks": res["clocks"],
     }
