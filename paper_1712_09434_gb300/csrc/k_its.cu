@@ -17,6 +17,8 @@ namespace tpc {
 namespace {
 
 constexpr int ITS_NPHI = 360;            // azimuth bins of the ITS track grid
+constexpr int ITS_NTL = 12;              // tan lambda bins of 0.2 over [-1.2, 1.2) (outside: the end bins)
+constexpr int ITS_NBINS = ITS_NPHI * ITS_NTL;
 constexpr double ITS_SIGMA_Y = 0.01;     // y of an ITS track at the vertex (cm)
 constexpr double ITS_DPHI = 0.1;         // candidate window in azimuth (rad)
 constexpr double ITS_DTL = 0.1;          // candidate window in tan lambda
@@ -32,6 +34,11 @@ constexpr double TWO_PI = 6.283185307179586;
 // a - 2 pi n with n the nearest integer (IEEE remainder, exact): [-pi, pi]; no loop, so a corrupt
 // angle cannot stall the kernel.  |a| <= pi is its own remainder, so that case skips the call.
 __device__ __forceinline__ double wrap_pi(double a) { return fabs(a) <= 0.5 * TWO_PI ? a : remainder(a, TWO_PI); }
+
+__device__ __forceinline__ int tl_bin(float tl) {
+    const int b = (int)floorf((tl + 1.2f) * 5.0f);
+    return b < 0 ? 0 : (b >= ITS_NTL ? ITS_NTL - 1 : b);
+}
 
 __device__ __forceinline__ int phi_bin(double phi) {
     int b = (int)floor(phi / TWO_PI * ITS_NPHI);
@@ -53,7 +60,7 @@ struct ItsArgs {
 __global__ void k_its_count(Work W, ItsArgs A) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_its; i += gridDim.x * blockDim.x) {
         const double phi = A.its[8 * (size_t)i];
-        atomicAdd(A.cnt + phi_bin(phi), 1);
+        atomicAdd(A.cnt + phi_bin(phi) * ITS_NTL + tl_bin(A.its[8 * (size_t)i + 2]), 1);
         A.sc[2 * (size_t)i] = sin(phi);
         A.sc[2 * (size_t)i + 1] = cos(phi);
         A.best_its[i] = ~0ull;
@@ -63,7 +70,7 @@ __global__ void k_its_count(Work W, ItsArgs A) {
 
 __global__ void k_its_fill(Work W, ItsArgs A) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_its; i += gridDim.x * blockDim.x) {
-        const int b = phi_bin(A.its[8 * (size_t)i]);
+        const int b = phi_bin(A.its[8 * (size_t)i]) * ITS_NTL + tl_bin(A.its[8 * (size_t)i + 2]);
         A.list[A.off[b] + atomicAdd(A.fill + b, 1)] = i;
     }
 }
@@ -93,8 +100,9 @@ __device__ double chi2_4(double M[4][4], const double d[4]) {
     return c2;
 }
 
-// Thread per TPC track: its state at the vertex, then the ITS tracks of the azimuth bins within the
-// window; the best (key, ITS index) kept, (key, track) offered to the ITS track.
+// Thread per TPC track: its state at the vertex, then the ITS tracks of the (azimuth, tan lambda)
+// bins that reach into the window; the best (key, ITS index) kept, (key, track) offered to the ITS
+// track.
 __global__ void k_its_match(Work W, ItsArgs A) {
     const DevGeom &g = *W.geom;
     const int nt = min(*W.n_tracks, W.cap_tracks);
@@ -131,16 +139,39 @@ __global__ void k_its_match(Work W, ItsArgs A) {
         const double phi_t = alpha + asin(s.p[2]);
         const double sa = sin(alpha), ca = cos(alpha);
         const float tl32 = (float)s.p[3], z32 = (float)s.p[1];
+        // FP32 copies for the pre-checks below
+        const float phi32 = (float)phi_t, sa32 = (float)sa, ca32 = (float)ca;
+        const float d0_32 = (float)s.p[0], sn32 = (float)s.p[2], q32 = (float)s.p[4];
+        const float m0_32 = (float)(s.P[0][0] + ITS_SIGMA_Y * ITS_SIGMA_Y), pss32 = (float)s.P[2][2];
+        const float ptt32 = (float)s.P[3][3], pqq32 = (float)s.P[4][4];
         const int ix[4] = {0, 2, 3, 4};
         unsigned long long best = ~0ull;
         const int b0 = (int)floor((phi_t - ITS_DPHI) / TWO_PI * ITS_NPHI), b1 = (int)floor((phi_t + ITS_DPHI) / TWO_PI * ITS_NPHI);
         for (int bb = b0; bb <= b1; bb++) {
-            const int b = ((bb % ITS_NPHI) + ITS_NPHI) % ITS_NPHI;
-            for (int j = A.off[b]; j < A.off[b + 1]; j++) {
+            const int bp = ((bb % ITS_NPHI) + ITS_NPHI) % ITS_NPHI;
+            // the tan lambda bins that can hold an ITS track within the window (and its margin)
+            const int j0 = A.off[bp * ITS_NTL + tl_bin(tl32 - (float)ITS_DTL - 2e-3f)];
+            const int j1 = A.off[bp * ITS_NTL + tl_bin(tl32 + (float)ITS_DTL + 2e-3f) + 1];
+            for (int j = j0; j < j1; j++) {
                 const int i = A.list[j];
                 const float *r = A.its + 8 * (size_t)i;
                 // FP32 pre-checks with a margin that the exact tests below can only narrow
                 if (fabsf(r[2] - tl32) > (float)ITS_DTL + 1e-3f || fabsf(r[1] - z32) > (float)ITS_DZ + 1e-3f) continue;
+                {
+                    // the azimuth window and the one-component chi2 bound below, in FP32 with margins
+                    // (1e-3 rad; 0.1 % of the bound) far above FP32 rounding: they only reject pairs
+                    // that the FP64 tests reject too
+                    float dph = r[0] - phi32;
+                    dph -= rintf(dph * (float)(1.0 / TWO_PI)) * (float)TWO_PI;
+                    if (fabsf(dph) > (float)ITS_DPHI + 1e-3f) continue;
+                    const float s0 = (float)A.sc[2 * (size_t)i], c0 = (float)A.sc[2 * (size_t)i + 1];
+                    const float sdp = s0 * ca32 - c0 * sa32, cph = (c0 * ca32 + s0 * sa32) * r[4];
+                    const float d1 = sn32 - sdp, d2 = tl32 - r[2], d3 = q32 - r[3];
+                    const float g = (float)ITS_CHI2 * 1.001f;
+                    if (d0_32 * d0_32 > g * m0_32 || d1 * d1 > g * (pss32 + cph * cph) ||
+                        d2 * d2 > g * (ptt32 + r[6] * r[6]) || d3 * d3 > g * (pqq32 + r[7] * r[7]))
+                        continue;
+                }
                 if (fabs(wrap_pi((double)r[0] - phi_t)) > ITS_DPHI) continue;
                 if (fabs((double)r[2] - s.p[3]) > ITS_DTL || fabs((double)r[1] - s.p[1]) > ITS_DZ) continue;
                 // sin, cos of phi0 - alpha from those of phi0 and alpha (no transcendental per pair)
@@ -149,6 +180,13 @@ __global__ void k_its_match(Work W, ItsArgs A) {
                 const double d[4] = {s.p[0], s.p[2] - sdp, s.p[3] - (double)r[2], s.p[4] - (double)r[3]};
                 const double cph = cdp * (double)r[4];
                 const double ev[4] = {ITS_SIGMA_Y * ITS_SIGMA_Y, cph * cph, (double)r[6] * r[6], (double)r[7] * r[7]};
+                // d^T M^-1 d >= d_a^2 / M_aa for a positive definite M (Cauchy-Schwarz): one component
+                // beyond the gate on its own, with a margin far above the rounding of the
+                // factorisation, rejects the pair without it (the same decision)
+                bool beyond = false;
+                for (int a = 0; a < 4; a++)
+                    beyond |= d[a] * d[a] > ITS_CHI2 * (s.P[ix[a]][ix[a]] + ev[a]) * (1.0 + 1e-9);
+                if (beyond) continue;
                 double M[4][4];
                 for (int a = 0; a < 4; a++)
                     for (int c = 0; c < 4; c++) M[a][c] = s.P[ix[a]][ix[c]] + (a == c ? ev[a] : 0.0);
@@ -193,7 +231,7 @@ __global__ void k_its_link(Work W, ItsArgs A) {
 
 }  // namespace
 
-int its_match_nphi() { return ITS_NPHI; }
+int its_match_nphi() { return ITS_NBINS; }
 int its_constants(double *out) {
     const double v[] = {ITS_SIGMA_Y, ITS_DPHI, ITS_DTL, ITS_DZ, ITS_CHI2};
     for (int i = 0; i < 5; i++) out[i] = v[i];
@@ -222,10 +260,10 @@ void launch_its_match(const Work &W, const float *its, int n_its, int32_t *match
     A.best_its = W.gap_bestS;
     A.sc = reinterpret_cast<double *>(W.gap_state);   // 6 words per chain slot >= 2 doubles per ITS track
     const int grid = W.sm_count * 4;
-    cudaMemsetAsync(A.cnt, 0, sizeof(int32_t) * (ITS_NPHI + 1), s);
-    cudaMemsetAsync(A.fill, 0, sizeof(int32_t) * (ITS_NPHI + 1), s);
+    cudaMemsetAsync(A.cnt, 0, sizeof(int32_t) * (ITS_NBINS + 1), s);
+    cudaMemsetAsync(A.fill, 0, sizeof(int32_t) * (ITS_NBINS + 1), s);
     k_its_count<<<grid, 256, 0, s>>>(W, A);
-    scan_exclusive(A.cnt, A.off, ITS_NPHI, nullptr, nullptr, W.scan_tmp, W.scan_tmp_len, s);
+    scan_exclusive(A.cnt, A.off, ITS_NBINS, nullptr, nullptr, W.scan_tmp, W.scan_tmp_len, s);
     k_its_fill<<<grid, 256, 0, s>>>(W, A);
     k_its_match<<<grid, 128, 0, s>>>(W, A);
     k_its_link<<<grid, 256, 0, s>>>(W, A);
