@@ -33,6 +33,7 @@ struct LoopArgs {
     int32_t *pair, *leg;
     double kB, alpha0, dalpha;
     double *rec;                  // [nt][LOOP_REC]: cx, cy, R, far-point z, tan lambda, curvature sign, side
+    float4 *rec32;                // [nt][2]: (cx, cy, R, far-point z), (tan lambda, curvature sign, 0, 0)
     int32_t *key;                 // [nt] event * LOOP_NPHI + azimuth bin, -1 for a track that is no candidate
     int32_t *cnt, *off, *fill, *list;
     unsigned long long *best;     // [nt] (floor(D 2^20) << 32) | partner
@@ -93,6 +94,8 @@ __global__ void k_loop_prep(Work W, LoopArgs A) {
         r[4] = tl;
         r[5] = C > 0.0 ? 1.0 : -1.0;
         r[6] = k < g.half ? 1.0 : -1.0;
+        A.rec32[2 * (size_t)t] = make_float4((float)cx, (float)cy, (float)R, (float)r[3]);
+        A.rec32[2 * (size_t)t + 1] = make_float4((float)tl, (float)r[5], 0.f, 0.f);
         int b = (int)floor(atan2(cy, cx) / TWO_PI * LOOP_NPHI);
         b %= LOOP_NPHI;
         if (b < 0) b += LOOP_NPHI;
@@ -116,6 +119,7 @@ __global__ void k_loop_match(Work W, LoopArgs A) {
         if (key < 0) continue;
         const double *ra = A.rec + (size_t)a * LOOP_REC;
         const double cx = ra[0], cy = ra[1], R = ra[2], zap = ra[3], tl = ra[4], sg = ra[5];
+        const float4 fa = A.rec32[2 * (size_t)a], ga = A.rec32[2 * (size_t)a + 1];
         const int e0 = key - key % LOOP_NPHI, b0 = key % LOOP_NPHI;
         unsigned long long best = ~0ull;
         for (int db = -1; db <= 1; db++) {
@@ -123,6 +127,16 @@ __global__ void k_loop_match(Work W, LoopArgs A) {
             for (int j = A.off[bin]; j < A.off[bin + 1]; j++) {
                 const int b = A.list[j];
                 if (b == a) continue;
+                {   // FP32 pre-checks with margins far above FP32 rounding (coordinates up to a few
+                    // hundred cm): they only reject pairs that the FP64 tests below reject
+                    const float4 fb = A.rec32[2 * (size_t)b], gb = A.rec32[2 * (size_t)b + 1];
+                    if (gb.y == ga.y) continue;
+                    const float ex = fa.x - fb.x, ey = fa.y - fb.y;
+                    if (ex * ex + ey * ey > (float)((LOOP_DC + 1e-2) * (LOOP_DC + 1e-2)) ||
+                        fabsf(fa.z - fb.z) > (float)(LOOP_DR + 1e-2) || fabsf(fa.w - fb.w) > (float)(LOOP_DZ + 1e-2) ||
+                        fabsf(ga.x + gb.x) > (float)(LOOP_DTL + 1e-4))
+                        continue;
+                }
                 const double *rb = A.rec + (size_t)b * LOOP_REC;
                 if (rb[5] == sg) continue;
                 const double dx = cx - rb[0], dy = cy - rb[1];
@@ -172,6 +186,7 @@ void launch_looper_pairs(const Work &W, int32_t *pair, int32_t *leg, double kB, 
     A.alpha0 = alpha0;
     A.dalpha = dalpha;
     A.rec = rec;
+    A.rec32 = reinterpret_cast<float4 *>(rec + (size_t)nt_cap * LOOP_REC);
     A.nt_cap = nt_cap;
     // workspace of the tracking, free between calls: bin counts, offsets, fill levels, the sorted
     // candidate list, the bin key and the best key of every track

@@ -525,8 +525,8 @@ int tpc_looper_pairs(tpc_ctx *c, const tpc_clusters *in, const tpc_tracks *trk, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TPC_CUDA(cudaMemsetAsync(W.counters + CNT_BINS_BAD, 0, sizeof(int32_t), s));
     launch_bins_check(W, s);
-    // candidate records (8 doubles per track) in the refit workspace, which is free between calls
-    const long long rec_tracks = (long long)refit_ck_words((long long)c->max_clusters + 1, (long long)c->cap_chains + 1) / 16;
+    // candidate records (8 doubles and 8 floats per track) in the refit workspace, free between calls
+    const long long rec_tracks = (long long)refit_ck_words((long long)c->max_clusters + 1, (long long)c->cap_chains + 1) / 24;
     const int nt_cap = (int)std::min<long long>(c->cap_chains, rec_tracks);
     const double ha = c->geom.half_angle_deg * M_PI / 180.0;
     launch_looper_pairs(W, pair, leg, -0.299792458e-2 * c->bz, ha, 2.0 * ha, reinterpret_cast<double *>(c->ck),
