@@ -282,8 +282,18 @@ def test_repeated_runs_are_bitwise_identical(ctx):
 def test_degenerate_inputs(ctx):
     # empty event
     empty = synth.make_event(synth.EventConfig(n_tracks=0, noise_frac=0.0, seed=1))
-    g = _gpu.run(ctx, _gpu.clusters_of(empty))
+    cl_empty = _gpu.clusters_of(empty)
+    g = _gpu.run(ctx, cl_empty)
     assert g["n_tracks"] == 0
+    # the matching steps on no tracks: nothing paired or matched, no error
+    pair = torch.full((4,), 77, dtype=torch.int32, device="cuda")
+    ctx.tpc_looper_pairs(cl_empty, g["tracks_obj"], pair)
+    its = torch.zeros((3, 8), dtype=torch.float32, device="cuda")
+    mt = torch.full((4,), 77, dtype=torch.int32, device="cuda")
+    mi = torch.full((3,), 77, dtype=torch.int32, device="cuda")
+    ctx.tpc_its_match(cl_empty, g["tracks_obj"], its, mt, mi)
+    assert ctx.tpc_sync_status() == 0
+    assert bool((pair == 77).all()) and bool((mt == 77).all()) and bool((mi == -1).all())
     # noise only: the oracle decides what (if anything) is a track; the GPU must agree
     cfg = synth.EventConfig(n_tracks=50, noise_frac=0.0, seed=2)
     ev = synth.make_event(cfg)
