@@ -600,20 +600,26 @@ __global__ void __launch_bounds__(RED_T) k_reduce_records(Work W, const float *r
     }
 }
 
-// Sum of the block partials: one warp per column, lane l takes blocks l, l+32, ... in order and
-// the lanes combine with a fixed butterfly, so the result does not depend on timing.
-__global__ void k_reduce_final(Work W, int np, const double *part, double *sum_chi2, double *grad) {
+// Sum of the block partials: one block per column; thread i takes blocks i, i + 256, ... in order,
+// then a fixed tree in shared memory, so the result does not depend on timing.
+constexpr int RED_FINAL_T = 256;
+__global__ void __launch_bounds__(RED_FINAL_T) k_reduce_final(Work W, int np, const double *part, double *sum_chi2,
+                                                             double *grad) {
+    __shared__ double acc[RED_FINAL_T];
     const int nt = n_tracks_of(W);
     const int nb = (nt + RED_T - 1) / RED_T;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j <= np; j += nw) {
-        double acc = 0.0;
-        for (int b = lane; b < nb; b += 32) acc += part[(size_t)b * (np + 1) + j];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            if (j == np) *sum_chi2 = acc;
-            else if (grad) grad[j] = acc;
-        }
+    const int j = blockIdx.x;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb; b += RED_FINAL_T) a += part[(size_t)b * (np + 1) + j];
+    acc[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = RED_FINAL_T / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) acc[threadIdx.x] += acc[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (j == np) *sum_chi2 = acc[0];
+        else if (grad) grad[j] = acc[0];
     }
 }
 
@@ -763,7 +769,7 @@ void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, con
     const int cap = W.cap_tracks < W.cap_chains ? W.cap_tracks : W.cap_chains;
     const int nb = (cap + RED_T - 1) / RED_T;
     k_reduce_records<<<nb > 0 ? nb : 1, RED_T, 0, s>>>(W, rec, part);
-    k_reduce_final<<<1, 1024, 0, s>>>(W, 1 + 2 * W.ns, part, sum_chi2, grad);
+    k_reduce_final<<<2 + 2 * W.ns, RED_FINAL_T, 0, s>>>(W, 1 + 2 * W.ns, part, sum_chi2, grad);
 }
 
 }  // namespace tpc
