@@ -628,11 +628,16 @@ __global__ void __launch_bounds__(RED_FINAL_T) k_reduce_final(Work W, int np, co
 // ones start first.  The order inside a bucket does not matter (every track is independent).
 constexpr int LEN_BUCKETS = 512;
 
+// The lanes of a warp with the same bucket add to it with one atomic (tracks of similar length are
+// common, and one atomic per track serialised on the popular buckets).
 __global__ void k_len_hist(Work W, int32_t *hist) {
     const int nt = n_tracks_of(W);
+    const int lane = threadIdx.x & 31;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const int n = W.trk_off[t + 1] - W.trk_off[t];
-        atomicAdd(hist + (LEN_BUCKETS - 1 - min(max(n, 0), LEN_BUCKETS - 1)), 1);
+        const int b = LEN_BUCKETS - 1 - min(max(n, 0), LEN_BUCKETS - 1);
+        const unsigned peers = __match_any_sync(__activemask(), b);
+        if (lane == __ffs(peers) - 1) atomicAdd(hist + b, __popc(peers));
     }
 }
 
@@ -653,10 +658,16 @@ __global__ void k_len_scan(int32_t *hist) {   // one block of LEN_BUCKETS thread
 
 __global__ void k_len_scatter(Work W, int32_t *hist, int32_t *order) {
     const int nt = n_tracks_of(W);
+    const int lane = threadIdx.x & 31;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const int n = W.trk_off[t + 1] - W.trk_off[t];
         const int b = LEN_BUCKETS - 1 - min(max(n, 0), LEN_BUCKETS - 1);
-        order[hist[b] + atomicAdd(hist + LEN_BUCKETS + b, 1)] = t;
+        const unsigned peers = __match_any_sync(__activemask(), b);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(hist + LEN_BUCKETS + b, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        order[hist[b] + base + __popc(peers & ((1u << lane) - 1u))] = t;
     }
 }
 
