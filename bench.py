@@ -35,11 +35,12 @@ from paper_1712_09434_gb300 import synth  # noqa: E402
 
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
 # kernels of one step (one graph): tracking (bin offset check 2, grid 1, links 1, chains 8, follow 1,
-# select 1, merge 17, refit 1) + refit and adjoint of its tracks (length sort 3, forward and reverse
-# pass 2, reduce 2; the stored-state form adds the chunk lengths and their scan, 4; the hits were
-# packed and the bin offsets checked by the tracking part)
-LAUNCHES_TRACKING = 32
-LAUNCHES_REFIT_GRAD = {"checkpoints": 7, "stored states": 11}
+# select 1, merge 17, length order of the tracks 3, refit 1) + refit and adjoint of its tracks
+# (forward and reverse pass 2, reduce 2; the stored-state form adds the chunk lengths and their
+# scan, 4; the hits were packed, the tracks sorted by length and the bin offsets checked by the
+# tracking part)
+LAUNCHES_TRACKING = 35
+LAUNCHES_REFIT_GRAD = {"checkpoints": 4, "stored states": 8}
 
 def launches_per_step(tuning_best):
     form = "stored states" if tuning_best and tuple(tuning_best.get("refit_grad", (0, 0, 0)))[2] == 1 else "checkpoints"

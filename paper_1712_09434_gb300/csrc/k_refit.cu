@@ -188,7 +188,9 @@ __device__ __forceinline__ int n_tracks_of(const Work &W) {
 }
 
 // S8 at the nominal calibration: parameters, covariance, chi2, ndf of every track.
-__global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
+// Tracks taken in the order of `order` (decreasing length) when given, so that the lanes of a warp
+// fit tracks of about the same length.
+__global__ void __launch_bounds__(128) k_refit(Work W, const float *theta, const int32_t *order) {
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
     const int ns = W.ns, np = 1 + 2 * ns;
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(128) k_refit(Work W, const float *theta) {
     FitGeo fg;
     load_geo(G, fg);
     const int nt = n_tracks_of(W);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+        const int t = order ? order[i] : i;
         const int off = W.trk_off[t];
         int n = W.trk_off[t + 1] - off;
         if (off < 0 || n < 0 || off + n > W.cap_hits) {   // hits beyond the packed range: not fitted
@@ -743,23 +746,27 @@ int refit_rec_words(int cap_tracks) { return cap_tracks * REC_WORDS; }
 int refit_part_doubles(int cap_tracks, int ns) { return ((cap_tracks + RED_T - 1) / RED_T + 1) * (2 * ns + 2); }
 
 
-void launch_refit(const Work &W, const float *theta, cudaStream_t s) {
+void launch_len_order(const Work &W, int32_t *order, int32_t *hist, cudaStream_t s) {
+    cudaMemsetAsync(hist, 0, sizeof(int32_t) * LEN_BUCKETS, s);
+    k_len_hist<<<W.sm_count * 4, 256, 0, s>>>(W, hist);
+    k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
+    k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
+}
+
+void launch_refit(const Work &W, const float *theta, const int32_t *order, cudaStream_t s) {
     const int block = W.tune.block[6] > 0 ? W.tune.block[6] : 128;
     const int grid = W.tune.grid[6] > 0 ? W.tune.grid[6] : W.sm_count * 8;
-    k_refit<<<grid, block, 0, s>>>(W, theta);
+    k_refit<<<grid, block, 0, s>>>(W, theta, order);
 }
 
 void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
                            bool grad, float *ck, long long ck_hits, long long ck_tracks, float *rec, int32_t *order,
-                           int32_t *hist, cudaStream_t s) {
+                           int32_t *hist, bool sorted, cudaStream_t s) {
     const int block = W.tune.block[7] > 0 ? W.tune.block[7] : 128;
     const int grid = W.tune.grid[7] > 0 ? W.tune.grid[7] : W.sm_count * 8;
     const CkLayout L = ck_layout(ck, ck_hits, ck_tracks);
-    cudaMemsetAsync(hist, 0, sizeof(int32_t) * LEN_BUCKETS, s);
     cudaMemsetAsync(W.counters + CNT_Q0 + 7, 0, sizeof(int32_t), s);
-    k_len_hist<<<W.sm_count * 4, 256, 0, s>>>(W, hist);
-    k_len_scan<<<1, LEN_BUCKETS, 0, s>>>(hist);
-    k_len_scatter<<<W.sm_count * 4, 256, 0, s>>>(W, hist, order);
+    if (!sorted) launch_len_order(W, order, hist, s);
     if (grad && W.tune.chunk[7] == 1) {     // every step's input state stored, no recomputation
         k_chunk_len<<<W.sm_count * 4, 256, 0, s>>>(W, order, L);
         scan_exclusive(L.cl, L.cb, (int)(ck_tracks / 32 + 1), L.cn, L.cn + 1, W.scan_tmp, W.scan_tmp_len, s);

@@ -216,7 +216,8 @@ int enqueue_pipeline(const tpc_ctx *c, const Work &W, cudaStream_t s, bool captu
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_pipe[5], s, evf));
     launch_merge(W, s);
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_pipe[6], s, evf));
-    launch_refit(W, c->theta0, s);
+    launch_len_order(W, c->order, c->lhist, s);
+    launch_refit(W, c->theta0, c->order, s);
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_pipe[7], s, evf));
     return cuda_err(cudaGetLastError());
 }
@@ -232,7 +233,8 @@ struct RefitArgs {
 // Refit under theta and its adjoint for the tracks counted in *n_tracks_dev (S0, S8, S9), enqueued
 // on s.  With profiling on, events between the refit stages (external event nodes when capturing).
 // pack = false when the tracking part of the same stream order has just checked the bin offsets
-// and written the packed hits of exactly these tracks (the whole step as one graph).
+// and written the packed hits and the length order of exactly these tracks (the whole step as one
+// graph).
 int enqueue_refit_grad(const tpc_ctx *c, const Work &W, const int32_t *n_tracks_dev, const double *theta,
                        const float *weight, const float *anchor, int model, double *sum_chi2, double *grad,
                        cudaStream_t s, bool capturing, bool pack = true) {
@@ -248,7 +250,7 @@ int enqueue_refit_grad(const tpc_ctx *c, const Work &W, const int32_t *n_tracks_
     }
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[1], s, evf));
     launch_refit_grad_fit(W, theta, weight, anchor, model, grad != nullptr, c->ck, (long long)c->max_clusters + 1,
-                          (long long)c->cap_chains + 1, c->rec, c->order, c->lhist, s);
+                          (long long)c->cap_chains + 1, c->rec, c->order, c->lhist, !pack, s);
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[2], s, evf));
     launch_refit_grad_reduce(W, sum_chi2, grad, c->rec, c->part, s);
     if (prof) TPC_CUDA(cudaEventRecordWithFlags(c->ev_refit[3], s, evf));

@@ -194,10 +194,13 @@ void launch_follow(const Work &W, cudaStream_t s);
 void launch_select(const Work &W, cudaStream_t s);
 void launch_merge(const Work &W, cudaStream_t s);
 void launch_frame_merge(const Work &W, cudaStream_t s);
-void launch_refit(const Work &W, const float *theta, cudaStream_t s);
+// tracks in order of decreasing hit count into order (hist: 2 * 512 words of scratch)
+void launch_len_order(const Work &W, int32_t *order, int32_t *hist, cudaStream_t s);
+void launch_refit(const Work &W, const float *theta, const int32_t *order, cudaStream_t s);
+// sorted: order already holds the length order of these tracks
 void launch_refit_grad_fit(const Work &W, const double *theta, const float *weight, const float *anchor, int model,
                            bool grad, float *ck, long long ck_hits, long long ck_tracks, float *rec, int32_t *order,
-                           int32_t *hist, cudaStream_t s);
+                           int32_t *hist, bool sorted, cudaStream_t s);
 void launch_refit_grad_reduce(const Work &W, double *sum_chi2, double *grad, const float *rec, double *part,
                               cudaStream_t s);
 size_t refit_ck_words(long long cap_hits, long long cap_tracks);
