@@ -637,7 +637,7 @@ def run_native(args, rank, world):
                 "of_them_joined": float(np.isin(both, joined).mean()) if both.size else None}
     th5 = torch.tensor(synth.calib_theta(1005), dtype=torch.float64, device=dev)
     # the adjoint as specified: per-row Kalman states recomputed in the reverse sweep from checkpoints
-    # (every 16 steps); then the variant that stores every step's input state (100 B per hit)
+    # (every 16 steps); then the variant that stores every step's input state (80 B per hit)
     from paper_1712_09434_gb300 import tune as _tune
     ms_grad, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5, a5, 1), 10, 3)
     g_ck = grad.clone()
@@ -793,7 +793,7 @@ def finish_native(args, res, world):
                     "form": "refit + adjoint, Kalman states of the reverse sweep recomputed from checkpoints "
                             "every 16 steps",
                     "stored_states": {"value": res["ms_grad_event_stored"] * 1e3, "unit": "us/event",
-                                      "form": "variant storing every step's input state (100 B per hit); "
+                                      "form": "variant storing every step's input state (80 B per hit); "
                                               "identical gradient"}},
         "calibration": res["calib"],
         "its_match": res.get("its_match"),

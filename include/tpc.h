@@ -100,7 +100,7 @@ typedef struct {
  * lanes taking the bin's clusters in Z-slab order), and chunk = 2 the warp-per-bin variant whose
  * lanes take the clusters in cluster (Y, Z) order; for the gradient kernel (index 7) the default
  * recomputes the Kalman states of the reverse sweep from checkpoints every 16 steps, and chunk = 1
- * selects the variant that stores the input state of every step instead (100 B per hit of
+ * selects the variant that stores the input state of every step instead (80 B per hit of
  * workspace, no recomputation; the same gradient bit for bit).
  * Launch shapes never change results. */
 typedef struct {

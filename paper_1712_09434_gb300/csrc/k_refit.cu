@@ -7,7 +7,7 @@
 // theta; the fit runs from the last hit to the first.  The adjoint's forward pass stores every K-th
 // state (checkpoints) and the reverse sweep recomputes each segment's states from its checkpoint
 // before walking it backwards; a variant stores the input state of every step instead (coalesced
-// by warp chunk, 100 B per hit) and walks them backwards without recomputation (same results, bit
+// by warp chunk, 80 B per hit) and walks them backwards without recomputation (same results, bit
 // for bit).  Per-track chi2 and gradient contributions
 // (s_vd, and (d_k, a_k) for every sector the track visits) are written as records and summed in
 // FP64 in a fixed order (deterministic).
@@ -21,6 +21,7 @@ namespace {
 constexpr int CK_K = 16;           // steps between checkpoints
 constexpr int ST_SLACK = 4096;     // spare steps per lane for the chunk padding of the stored states
 constexpr int CK_WORDS = 25;       // x, p[5], P lower triangle[15], frame, rref, yref, zref
+constexpr int ST_WORDS = 20;       // p[5], P lower triangle[15] (stored states: the rest from the hits)
 constexpr int REC_SEC = 8;         // sector entries per track record
 constexpr int REC_WORDS = 2 + 3 * REC_SEC;
 constexpr int NPAR_MAX = 1 + 2 * MAX_SECTORS;
@@ -40,7 +41,7 @@ inline size_t ck_words_old(long long cap_hits, long long cap_tracks) {
 }
 inline size_t ck_words_fin(long long cap_tracks) { return (size_t)cap_tracks * CK_WORDS; }
 inline size_t ck_words_ints(long long cap_tracks) { return (size_t)(3 * (cap_tracks / 32 + 2) + 8); }
-inline size_t ck_words_st(long long cap_hits) { return (size_t)(cap_hits + 32ll * ST_SLACK) * CK_WORDS; }
+inline size_t ck_words_st(long long cap_hits) { return (size_t)(cap_hits + 32ll * ST_SLACK) * ST_WORDS; }
 inline size_t ck_align(size_t w) { return (w + 31) & ~(size_t)31; }
 inline CkLayout ck_layout(float *base, long long cap_hits, long long cap_tracks) {
     CkLayout L;
@@ -350,39 +351,32 @@ __device__ __forceinline__ void ck_load(const float *src, kf::State<float> &s) {
 
 // Stored states (MODE 3/4): the input state of every step, interleaved by warp chunk so that the 32
 // lanes of a warp store and load each word with one coalesced access: word k of step q of the
-// track at position i of the length order lives at st[((cb[i/32] + q) * CK_WORDS + k) * 32 + i%32].
+// track at position i of the length order lives at st[((cb[i/32] + q) * ST_WORDS + k) * 32 + i%32].
+// Only p and the covariance are stored: the input state of a step is referred to the hit of the
+// step before it (x, row, nominal y and z, sector), and that of the first step to its own hit (the
+// seed), so the reverse sweep takes them from that hit again.
 __device__ __forceinline__ void st_store(float *st, long long step, int lane, const kf::State<float> &s) {
-    float *d = st + step * (CK_WORDS * 32) + lane;
-    d[0] = s.x;
-    for (int i = 0; i < 5; i++) d[(1 + i) * 32] = s.p[i];
-    int m = 6;
+    float *d = st + step * (ST_WORDS * 32) + lane;
+    for (int i = 0; i < 5; i++) d[i * 32] = s.p[i];
+    int m = 5;
     for (int i = 0; i < 5; i++)
         for (int j = 0; j <= i; j++) d[(m++) * 32] = s.P[i][j];
-    d[21 * 32] = __int_as_float(s.frame);
-    d[22 * 32] = __int_as_float(s.rref);
-    d[23 * 32] = s.yref;
-    d[24 * 32] = s.zref;
 }
 __device__ __forceinline__ void st_load(const float *st, long long step, int lane, kf::State<float> &s) {
-    const float *d = st + step * (CK_WORDS * 32) + lane;
-    s.x = d[0];
-    for (int i = 0; i < 5; i++) s.p[i] = d[(1 + i) * 32];
-    int m = 6;
+    const float *d = st + step * (ST_WORDS * 32) + lane;
+    for (int i = 0; i < 5; i++) s.p[i] = d[i * 32];
+    int m = 5;
     for (int i = 0; i < 5; i++)
         for (int j = 0; j <= i; j++) {
             s.P[i][j] = d[m * 32];
             s.P[j][i] = d[m * 32];
             m++;
         }
-    s.frame = __float_as_int(d[21 * 32]);
-    s.rref = __float_as_int(d[22 * 32]);
-    s.yref = d[23 * 32];
-    s.zref = d[24 * 32];
 }
 
 // S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
 // MODE 0: forward pass only (objective).  Gradient, default: MODE 3 runs the forward pass and stores
-// the input state of every step (100 B per hit, coalesced by warp chunk) and the state after the
+// the input state of every step (80 B per hit, coalesced by warp chunk) and the state after the
 // last hit (frame -1 marks a track whose fit failed); MODE 4 runs the reverse sweep from the stored
 // states.  Gradient with less workspace: MODE 1 stores a checkpoint every CK_K steps, and MODE 2
 // recomputes each segment's states from its checkpoint before sweeping it backwards.  Both give
@@ -543,6 +537,14 @@ __global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0
                 if (q > 0) hb = hit_raw(W, off + n - q);
                 kf::State<float> sin_;
                 st_load(L.st, step0 + q, slane, sin_);
+                // the reference of the step's input state: the hit of the step before, or the seed's hit
+                const HitRaw &ref = q > 0 ? hb : h;
+                const HitT mr = transform(G, th, ns, ref, model);
+                sin_.x = mr.f.xl;
+                sin_.rref = ref.r;
+                sin_.yref = mr.f.yn;
+                sin_.zref = mr.f.zn;
+                sin_.frame = ref.k;
                 bwd_step(q, h, sin_);
             }
         }
