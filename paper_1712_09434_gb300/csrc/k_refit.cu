@@ -374,6 +374,25 @@ __device__ __forceinline__ void st_load(const float *st, long long step, int lan
         }
 }
 
+// p and the covariance of a state (20 words; the reference fields are rebuilt from a hit with
+// refer_to, as for the stored states)
+__device__ __forceinline__ void pp_store(float *d, const kf::State<float> &s) {
+    for (int i = 0; i < 5; i++) d[i] = s.p[i];
+    int m = 5;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) d[m++] = s.P[i][j];
+}
+__device__ __forceinline__ void pp_load(const float *d, kf::State<float> &s) {
+    for (int i = 0; i < 5; i++) s.p[i] = d[i];
+    int m = 5;
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j <= i; j++) {
+            s.P[i][j] = d[m];
+            s.P[j][i] = d[m];
+            m++;
+        }
+}
+
 // S8 + S9: refit under theta; per-track record [chi2, d/ds_vd, (sector, d/dd_k, d/da_k) x 8].
 // MODE 0: forward pass only (objective).  Gradient, default: MODE 3 runs the forward pass and stores
 // the input state of every step (80 B per hit, coalesced by warp chunk) and the state after the
@@ -507,7 +526,7 @@ __global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0
             ga.add((xb * m.xr + yb * m.yraw + (model == 1 ? vyb * (2.f * SIGMA2) * m.jy : 0.f)) * m.gp);
         };
         if constexpr (MODE == 2) {      // segment by segment from the last checkpoint
-            float buf[CK_K * CK_WORDS];     // recomputed step inputs of one segment (compact form)
+            float buf[CK_K * ST_WORDS];     // recomputed step inputs of one segment (p and covariance)
             for (int q0 = ((n - 1) / CK_K) * CK_K; q0 >= 0; q0 -= CK_K) {
                 const int q1 = min(q0 + CK_K, n);
                 kf::State<float> st;
@@ -517,7 +536,7 @@ __global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0
                 for (int q = q0; q < q1; q++) {
                     const HitRaw cur = nx;
                     if (q + 1 < q1) nx = hit_raw(W, off + n - 2 - q);
-                    ck_store(buf + (q - q0) * CK_WORDS, st);
+                    pp_store(buf + (q - q0) * ST_WORDS, st);
                     const HitT m = transform(G, th, ns, cur, model);
                     kf::step_fwd(st, m.f, fg.g, dummy);
                 }
@@ -526,7 +545,16 @@ __global__ void __launch_bounds__(128, (MODE == 2 || MODE == 4) ? 4 : (MODE == 0
                     const HitRaw h = hb;
                     if (q > q0) hb = hit_raw(W, off + n - q);
                     kf::State<float> sin_;
-                    ck_load(buf + (q - q0) * CK_WORDS, sin_);
+                    pp_load(buf + (q - q0) * ST_WORDS, sin_);
+                    // the reference of the step's input state: the hit of the step before, or the
+                    // seed's own hit for the first step
+                    const HitRaw ref = q > q0 ? hb : (q > 0 ? hit_raw(W, off + n - q) : h);
+                    const HitT mr = transform(G, th, ns, ref, model);
+                    sin_.x = mr.f.xl;
+                    sin_.rref = ref.r;
+                    sin_.yref = mr.f.yn;
+                    sin_.zref = mr.f.zn;
+                    sin_.frame = ref.k;
                     bwd_step(q, h, sin_);
                 }
             }
