@@ -190,8 +190,9 @@ __device__ __forceinline__ int n_tracks_of(const Work &W) {
 
 // S8 at the nominal calibration: parameters, covariance, chi2, ndf of every track.
 // Tracks taken in the order of `order` (decreasing length) when given, so that the lanes of a warp
-// fit tracks of about the same length.
-__global__ void __launch_bounds__(128) k_refit(Work W, const float *theta, const int32_t *order) {
+// fit tracks of about the same length.  Eight blocks a multiprocessor cap it at 64 registers a
+// thread (a few spilled words): more resident warps hide the latency of the filter's FMA chain.
+__global__ void __launch_bounds__(128, 8) k_refit(Work W, const float *theta, const int32_t *order) {
     __shared__ float th[NPAR_MAX];
     const DevGeom &G = *W.geom;
     const int ns = W.ns, np = 1 + 2 * ns;
