@@ -41,6 +41,9 @@ METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-gra
 # tracking part)
 LAUNCHES_TRACKING = 35
 LAUNCHES_REFIT_GRAD = {"checkpoints": 4, "stored states": 8}
+# copies of the central calibration event whose refit + adjoint run in one call (cost per event
+# when the gradient is summed over several events)
+CENTRAL_COPIES = 8
 
 def launches_per_step(tuning_best):
     form = "stored states" if tuning_best and tuple(tuning_best.get("refit_grad", (0, 0, 0)))[2] == 1 else "checkpoints"
@@ -645,6 +648,27 @@ def run_native(args, rank, world):
     ms_grad_stored, _ = timed(lambda: ctx.tpc_refit_grad(c5, t5, th5, s_chi2, grad, w5, a5, 1), 10, 3)
     ctx.tpc_set_tuning(None)
     assert torch.equal(g_ck, grad), "the two adjoint forms must give identical gradients"
+    # the same refit + adjoint over K copies of the event tracked as one batch, in one call: the
+    # cost per event when the calibration sums its gradient over several events (one event alone
+    # fills about one warp per SM sub-partition, so its time is the latency of its longest tracks)
+    K = CENTRAL_COPIES
+    bK = synth.concat_events([ev5] * K)
+    cK = capi.Clusters.from_numpy(bK.pad_fp, bK.time_fp, bK.bin_off, K)
+    tK = capi.Tracks(bK.n_clusters, K, K * (ev5.n_clusters // 8 + 1024), bK.n_clusters)
+    ctx.tpc_track_batch(cK, tK)
+    hK = tK.to_host()
+    assert hK["n_tracks"] == K * nt5 and np.array_equal(
+        hK["trk_hits"], np.concatenate([h5["trk_hits"] + e * ev5.n_clusters for e in range(K)])), \
+        "the copies must give the event's tracks"
+    wK, aK = w5.repeat(K), a5.repeat(K, 1)
+    gK = torch.empty_like(grad)
+    ms_grad_K, _ = timed(lambda: ctx.tpc_refit_grad(cK, tK, th5, s_chi2, gK, wK, aK, 1), 10, 3)
+    assert torch.allclose(gK, K * g_ck, rtol=1e-9, atol=1e-9 * float(g_ck.abs().max())), \
+        "K copies must give K times the event's gradient"
+    ctx.tpc_set_tuning(_tune.to_struct({"refit_grad": (0, 0, 1)}))
+    ms_grad_K_stored, _ = timed(lambda: ctx.tpc_refit_grad(cK, tK, th5, s_chi2, gK, wK, aK, 1), 10, 3)
+    ctx.tpc_set_tuning(None)
+    del cK, tK, bK
 
     # plain per-event tracking of single events: the central event above and a 5,000-track event
     single = {}
@@ -691,7 +715,8 @@ def run_native(args, rank, world):
                  "sum_chi2_start_end": [cres.history[0][1], cres.history[-1][1]],
                  "tracks_with_reference": int((ref5[:, 0] > 0).sum())}
 
-    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, ms_grad_event_stored=ms_grad_stored, its_match=match_out, loopers=loop_out,
+    out.update(ms_plain=ms_plain, ms_grad_event=ms_grad, ms_grad_event_stored=ms_grad_stored,
+               ms_grad_copies=ms_grad_K, ms_grad_copies_stored=ms_grad_K_stored, its_match=match_out, loopers=loop_out,
                inefficient=rules_out,
                n_tracks_c5=int(t5.n_tracks.item()), prof=prof,
                weighted_hits=weighted_hits,
@@ -794,7 +819,14 @@ def finish_native(args, res, world):
                             "every 16 steps",
                     "stored_states": {"value": res["ms_grad_event_stored"] * 1e3, "unit": "us/event",
                                       "form": "variant storing every step's input state (80 B per hit); "
-                                              "identical gradient"}},
+                                              "identical gradient"},
+                    "batched": {"value": res["ms_grad_copies"] * 1e3 / CENTRAL_COPIES, "unit": "us/event",
+                                "events": CENTRAL_COPIES,
+                                "stored_states": res["ms_grad_copies_stored"] * 1e3 / CENTRAL_COPIES,
+                                "form": "%d copies of the event tracked as one batch, refit + adjoint of all "
+                                        "their tracks in one call (checkpoints; stored_states: the variant); "
+                                        "gradient checked to be %d times the event's" % (CENTRAL_COPIES,
+                                                                                          CENTRAL_COPIES)}},
         "calibration": res["calib"],
         "its_match": res.get("its_match"),
         "looper_legs": res.get("loopers"),

@@ -17,7 +17,7 @@ def fake_result():
         "n_tracks": 218_000, "n_hits": 26_000_000, "weighted_hits": 25_000_000, "n_chains": 790_000,
         "cand_hits": 68_000_000, "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5},
         "tuning": {"key": "k", "source": "cache"}, "prof": ({k: v * n_calls for k, v in ms.items()}, n_calls),
-        "ms_plain": 114.0, "ms_grad_event": 1.2, "ms_grad_event_stored": 1.0, "n_tracks_c5": 25_779, "calib": {}, "single": {},
+        "ms_plain": 114.0, "ms_grad_event": 1.2, "ms_grad_event_stored": 1.0, "ms_grad_copies": 2.0, "ms_grad_copies_stored": 1.8, "n_tracks_c5": 25_779, "calib": {}, "single": {},
         "frame": {"value": 1.5e9}, "h2d": 134_324_888, "d2h": 365_388_892, "ms_e2e": 12.7, "ms_e2e_seq": 15.4,
     }
 

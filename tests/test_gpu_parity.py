@@ -400,3 +400,32 @@ def test_whole_step_graph_equals_the_two_calls(ctx):
         for k in ("trk_off", "trk_hits", "label", "par", "cov", "chi2", "ndf"):
             np.testing.assert_array_equal(h[k], g0[k], err_msg=k)
         assert torch.equal(s1, s0) and torch.equal(gr1, gr0)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_gradient_of_event_copies_is_the_sum(ctx, form):
+    """Several copies of one event tracked as one batch and refit in one call: the copies give the
+    event's tracks, and the sum of chi2 and the gradient are the copies' count times the event's,
+    in both forms of the adjoint (checkpoints, stored states); the FP64 sums over tracks differ
+    only in their order."""
+    from paper_1712_09434_gb300 import capi, tune
+    ev = _events.event("c2")
+    K = 3
+    th = synth.calib_theta(1005)
+    ctx.tpc_set_tuning(tune.to_struct({"refit_grad": (0, 0, form)}) if form else None)
+    try:
+        cl1 = _gpu.clusters_of(ev)
+        g1 = _gpu.run(ctx, cl1)
+        w1 = np.ones(g1["n_tracks"])
+        s1, gr1 = _refit_sum_grad(ctx, cl1, g1["tracks_obj"], th, w1)
+        b = synth.concat_events([ev] * K)
+        clK = _gpu.clusters_of(b, K)
+        gK = _gpu.run(ctx, clK, n_events=K, batch=True)
+        assert gK["n_tracks"] == K * g1["n_tracks"]
+        np.testing.assert_array_equal(
+            gK["trk_hits"], np.concatenate([g1["trk_hits"] + e * ev.n_clusters for e in range(K)]))
+        sK, grK = _refit_sum_grad(ctx, clK, gK["tracks_obj"], th, np.tile(w1, K))
+    finally:
+        ctx.tpc_set_tuning(None)
+    assert abs(sK - K * s1) <= 1e-12 * K * abs(s1)
+    np.testing.assert_allclose(grK, K * gr1, rtol=1e-10, atol=1e-10 * np.abs(K * gr1).max())
