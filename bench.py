@@ -34,12 +34,12 @@ sys.path.insert(0, ROOT)
 from paper_1712_09434_gb300 import synth  # noqa: E402
 
 METRIC = "TPC clusters/s tracked on 1 GB300, batched vs plain; adjoint calib-grad us/event"
-# kernels of one step (one graph): tracking (bin offset check 2, grid 1, links 1, chains 8, follow 1,
+# kernels of one step (one graph): tracking (bin offset check 2, grid 1, links 1, chains 8, follow 2,
 # select 1, merge 17, length order of the tracks 3, refit 1) + refit and adjoint of its tracks
 # (forward and reverse pass 2, reduce 2; the stored-state form adds the chunk lengths and their
 # scan, 4; the hits were packed, the tracks sorted by length and the bin offsets checked by the
 # tracking part)
-LAUNCHES_TRACKING = 35
+LAUNCHES_TRACKING = 36
 LAUNCHES_REFIT_GRAD = {"checkpoints": 4, "stored states": 8}
 # copies of the central calibration event whose refit + adjoint run in one call (cost per event
 # when the gradient is summed over several events)

@@ -7,7 +7,8 @@
 // The filter runs along the whole chain, then extends it row by row outwards, then (re-initialised
 // from the other end) inwards: predict, look up the nearest cluster (minimum (d^2, index)) within a
 // radius that grows with consecutive misses in the row's Z-slab grid, update.  A candidate is
-// stored as one cluster per row (-1 for a miss) between its first and last row.
+// stored as one cluster per row (-1 for a miss) between its first and last row.  The chains are
+// taken in an order that groups chains of equal length and nearby start rows in a warp (below).
 #include "tpc_common.cuh"
 
 namespace tpc {
@@ -106,11 +107,58 @@ __device__ int extend(const Work &W, const DevGeom &g, Abg &fy, Abg &fz, int row
     return n;
 }
 
+// Order in which the following takes the chains: per (event, sector), by groups of 16 start rows
+// and inside a group by decreasing chain length (lengths of 63 and more together), so that the
+// lanes of a warp filter chains of about the same length from about the same row and leave the
+// chain at about the same time.  One block per (event, sector): a counting sort in shared memory.
+// The candidates are still written at the chains' own indices, so the order changes no result.
+constexpr int FO_ROWS = 16, FO_LEN = 64, FO_KEYS = (MAX_ROWS / FO_ROWS) * FO_LEN;
+__global__ void __launch_bounds__(256) k_follow_order(Work W, int32_t *perm) {
+    __shared__ int s_cnt[FO_KEYS];
+    const int nr = W.geom->n_rows, ns = W.geom->n_sectors;
+    int n_chains = W.counters[CNT_NCHAINS];
+    if (n_chains > W.cap_chains) n_chains = W.cap_chains;
+    const int nkeys = ((nr + FO_ROWS - 1) / FO_ROWS) * FO_LEN;
+    for (int it = blockIdx.x; it < W.n_events * ns; it += gridDim.x) {
+        const int b0 = it * nr;
+        const int t0 = min(W.chain_off[b0], n_chains), t1 = min(W.chain_off[b0 + nr], n_chains);
+        if (t1 <= t0) continue;      // the same for the whole block
+        for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_cnt[k] = 0;
+        __syncthreads();
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int key = ((W.chain_bin[t] - b0) / FO_ROWS) * FO_LEN + (FO_LEN - 1 - min(W.chain_len[t], FO_LEN - 1));
+            atomicAdd(&s_cnt[key], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {      // exclusive scan of the counts by one warp, in key order
+            int run = t0;
+            for (int k0 = 0; k0 < nkeys; k0 += 32) {
+                const int k = k0 + threadIdx.x;
+                const int v = k < nkeys ? s_cnt[k] : 0;
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (threadIdx.x >= o) x += y;
+                }
+                if (k < nkeys) s_cnt[k] = run + x - v;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        __syncthreads();
+        for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+            const int key = ((W.chain_bin[t] - b0) / FO_ROWS) * FO_LEN + (FO_LEN - 1 - min(W.chain_len[t], FO_LEN - 1));
+            perm[atomicAdd(&s_cnt[key], 1)] = t;
+        }
+        __syncthreads();
+    }
+}
+
 // Each warp takes 32 x chunk chains at a time from the queue (no CTA barrier: a warp whose chains
 // end early takes the next ones while the others still follow theirs).  SKIP: chains may skip a
 // row (the skip-row rule); the plain instantiation keeps the plain reading's registers.
 template <bool SKIP>
-__global__ void __launch_bounds__(128) k_follow(Work W) {
+__global__ void __launch_bounds__(128) k_follow(Work W, const int32_t *perm) {
     const DevGeom &g = *W.geom;
     const int nr = g.n_rows;
     const int lane = threadIdx.x & 31;
@@ -123,7 +171,8 @@ __global__ void __launch_bounds__(128) k_follow(Work W) {
         if (lane == 0) base = atomicAdd(q, chunk);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n_chains) break;
-        for (int t = base + lane; t < base + chunk && t < n_chains; t += 32) {
+        for (int q = base + lane; q < base + chunk && q < n_chains; q += 32) {
+            const int t = perm[q];
             const int start = W.chain_start[t], len = W.chain_len[t], bin = W.chain_bin[t];
             const int row0 = bin % nr;
             const int rowbase = bin - row0;
@@ -237,10 +286,13 @@ __global__ void __launch_bounds__(128) k_follow(Work W) {
 void launch_follow(const Work &W, cudaStream_t s) {
     const int block = W.tune.block[3] > 0 ? W.tune.block[3] : 128;
     const int grid = W.tune.grid[3] > 0 ? W.tune.grid[3] : W.sm_count * 8;
+    // the permutation lives in the selection states, which the selection writes before it reads
+    int32_t *perm = W.cstate;
+    k_follow_order<<<W.sm_count * 8, 256, 0, s>>>(W, perm);
     if (W.rules & TPC_RULE_SKIP_ROW)
-        k_follow<true><<<grid, block, 0, s>>>(W);
+        k_follow<true><<<grid, block, 0, s>>>(W, perm);
     else
-        k_follow<false><<<grid, block, 0, s>>>(W);
+        k_follow<false><<<grid, block, 0, s>>>(W, perm);
 }
 
 }  // namespace tpc
