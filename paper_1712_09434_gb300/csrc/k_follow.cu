@@ -108,11 +108,11 @@ __device__ int extend(const Work &W, const DevGeom &g, Abg &fy, Abg &fz, int row
 }
 
 // Order in which the following takes the chains: per (event, sector), by groups of 16 start rows
-// and inside a group by decreasing chain length (lengths of 63 and more together), so that the
+// and inside a group by decreasing chain length (lengths of 127 and more together), so that the
 // lanes of a warp filter chains of about the same length from about the same row and leave the
 // chain at about the same time.  One block per (event, sector): a counting sort in shared memory.
 // The candidates are still written at the chains' own indices, so the order changes no result.
-constexpr int FO_ROWS = 16, FO_LEN = 64, FO_KEYS = (MAX_ROWS / FO_ROWS) * FO_LEN;
+constexpr int FO_ROWS = 16, FO_LEN = 128, FO_KEYS = (MAX_ROWS / FO_ROWS) * FO_LEN;
 __global__ void __launch_bounds__(256) k_follow_order(Work W, int32_t *perm) {
     __shared__ int s_cnt[FO_KEYS];
     const int nr = W.geom->n_rows, ns = W.geom->n_sectors;
