@@ -41,6 +41,11 @@ def test_bench_line_has_every_contract_key_and_consistent_figures():
     assert "traffic" in r
     e = line["e2e"]
     assert e["value"] == pytest.approx(33e6 / 12.7e-3) and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
+    a = line["adjoint"]
+    assert a["value"] == pytest.approx(1200.0) and a["stored_states"]["value"] == pytest.approx(1000.0)
+    assert a["batched"]["events"] == bench.CENTRAL_COPIES
+    assert a["batched"]["value"] == pytest.approx(2000.0 / bench.CENTRAL_COPIES)
+    assert a["batched"]["stored_states"] == pytest.approx(1800.0 / bench.CENTRAL_COPIES)
     # no tuned shapes: the library default adjoint (states recomputed from checkpoints)
     assert line["adjoint_form_in_step"] == "checkpoints"
     assert line["gpu_launches"] == (bench.LAUNCHES_TRACKING + bench.LAUNCHES_REFIT_GRAD["checkpoints"]) * 40
